@@ -1,0 +1,440 @@
+"""Pins of the CPU oracle against facts fixed by the paper or by mathematics.
+
+Each test ties one oracle function to something other than itself: the
+worked example of Figure 3, the closed form of Theorem 3.1 (and the
+recursion in its proof, Appendix A.1), Corollaries 3.1.1 and 3.1.2,
+Lemma 3.2, the end points of the KMR curve (Eq. 1), exhaustive search,
+library routines (scipy distances, torch dtype conversions) and pure-Python
+brute force on tiny inputs.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate
+from scipy.spatial.distance import cdist
+
+import oracle
+from oracle import probe_mlp
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_fig3():
+    xs, cs, prim, spills = None, [], None, []
+    with open(os.path.join(GOLDEN, "fig3_worked_example.txt")) as f:
+        for line in f:
+            line = line.split("#")[0].split()
+            if not line:
+                continue
+            tag, vals = line[0], line[1:]
+            if tag == "x":
+                xs = np.array([float(v) for v in vals])
+            elif tag == "c":
+                cs.append([float(v) for v in vals])
+            elif tag == "primary":
+                prim = int(vals[0])
+            elif tag == "spill":
+                spills.append((float(vals[0]), int(vals[1]), float(vals[2]), float(vals[3])))
+    return xs, np.array(cs), prim, spills
+
+
+# ---------------------------------------------------------------- Figure 3
+
+def test_fig3_primary_and_spill_by_lambda():
+    x, C, prim, spills = _read_fig3()
+    pi, best, _ = oracle.primary_assign(x[None, :], C)
+    assert int(pi[0]) == prim
+    assert best[0] == pytest.approx(1.0, abs=1e-12)
+    r = x - C[prim]
+    for lam, want, l2, l3 in spills:
+        a = oracle.soar_assign(x[None, :], C, lam, 1)
+        assert a[0, 0] == prim
+        assert a[0, 1] == want, f"lambda={lam}"
+        assert oracle.soar_loss(x, C[1], r, lam) == pytest.approx(l2, abs=1e-9)
+        assert oracle.soar_loss(x, C[2], r, lam) == pytest.approx(l3, abs=1e-9)
+
+
+def test_fig3_crossover_lambda():
+    x, C, prim, _ = _read_fig3()
+    lam_star = 0.8397 / 0.605104
+    assert oracle.soar_assign(x[None, :], C, lam_star - 1e-6, 1)[0, 1] == 1
+    assert oracle.soar_assign(x[None, :], C, lam_star + 1e-6, 1)[0, 1] == 2
+
+
+# ------------------------------------------------ Theorem 3.1 and corollaries
+
+def _unit_sphere(n, d, seed):
+    g = np.random.default_rng(seed).standard_normal((n, d))
+    return g / np.linalg.norm(g, axis=1, keepdims=True)
+
+
+def _J(d, lam):
+    """integral over [0, pi] of |cos theta|^lambda sin^d theta (I_d without A)."""
+    return integrate.quad(lambda th: abs(math.cos(th)) ** lam * math.sin(th) ** d, 0, math.pi)[0]
+
+
+def _I(d, lam):
+    """I_d of Appendix A.1, A normalising the density of theta (prop. to sin^(d-2))."""
+    return _J(d, lam) / _J(d - 2, 0.0)
+
+
+@pytest.mark.parametrize("d", [8, 16, 64])
+@pytest.mark.parametrize("lam", [0.0, 1.0, 2.0])
+def test_recursion_of_I_d(d, lam):
+    # (d + lambda) I_d = (d - 1) I_{d-2}, derived by parts in Appendix A.1
+    assert (d + lam) * _J(d, lam) == pytest.approx((d - 1) * _J(d - 2, lam), rel=1e-7)
+
+
+@pytest.mark.parametrize("d", [8, 16])
+@pytest.mark.parametrize("lam", [0.0, 1.0, 2.0])
+def test_theorem_closed_form_monte_carlo(d, lam):
+    # E_q[|cos theta|^lambda <q, r'>^2] over uniform unit q equals
+    # I_d / (d-1) * (||r'||^2 + lambda ||proj_r r'||^2): the oracle's loss
+    # times that constant must match a Monte Carlo estimate for many r'.
+    q = _unit_sphere(400_000, d, 7)
+    rng = np.random.default_rng(11)
+    r = rng.standard_normal(d)
+    cos = q @ (r / np.linalg.norm(r))
+    w = np.abs(cos) ** lam
+    const = _I(d, lam) / (d - 1)
+    x = rng.standard_normal(d)
+    for _ in range(6):
+        rp = rng.standard_normal(d) * rng.uniform(0.2, 2.0)
+        # a component along r makes the penalty matter
+        rp += rng.uniform(-1.5, 1.5) * r / np.linalg.norm(r) * np.linalg.norm(rp)
+        mc = np.mean(w * (q @ rp) ** 2)
+        loss = oracle.soar_loss(x, x - rp, r, lam)
+        assert mc == pytest.approx(const * loss, rel=0.03)
+
+
+def test_lambda_zero_constant_is_one_over_d():
+    # with w = 1, E[<q, r'>^2] = ||r'||^2 / d, since E[q q^T] = I/d (Lemma 3.2's proof)
+    for d in (4, 10, 100):
+        assert _I(d, 0.0) / (d - 1) == pytest.approx(1.0 / d, rel=1e-9)
+
+
+def test_corollary_lambda_zero_is_second_nearest():
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((300, 12))
+    C = rng.standard_normal((40, 12))
+    a = oracle.soar_assign(X, C, 0.0, 1)
+    D = cdist(X, C, "sqeuclidean")
+    order = np.argsort(D, axis=1, kind="stable")
+    np.testing.assert_array_equal(a[:, 0], order[:, 0])
+    np.testing.assert_array_equal(a[:, 1], order[:, 1])
+
+
+def test_corollary_orthogonal_residual():
+    rng = np.random.default_rng(6)
+    for _ in range(20):
+        d = int(rng.integers(2, 40))
+        r = rng.standard_normal(d)
+        rp = rng.standard_normal(d)
+        rp -= (rp @ r) / (r @ r) * r          # r' orthogonal to r
+        x = rng.standard_normal(d)
+        for lam in (0.0, 0.7, 3.0):
+            assert oracle.soar_loss(x, x - rp, r, lam) == pytest.approx(rp @ rp, rel=1e-12)
+        # for fixed ||r'||, any parallel component raises the loss when lambda > 0
+        tilt = rp + 0.3 * r
+        tilt *= np.linalg.norm(rp) / np.linalg.norm(tilt)
+        assert oracle.soar_loss(x, x - tilt, r, 1.0) > oracle.soar_loss(x, x - rp, r, 1.0)
+
+
+def test_lemma_pearson_equals_cosine():
+    d = 12
+    q = _unit_sphere(300_000, d, 3)
+    rng = np.random.default_rng(4)
+    for _ in range(4):
+        r, rp = rng.standard_normal(d), rng.standard_normal(d)
+        rho = np.corrcoef(q @ r, q @ rp)[0, 1]
+        cos = r @ rp / np.linalg.norm(r) / np.linalg.norm(rp)
+        assert rho == pytest.approx(cos, abs=0.01)
+        # ||proj_r r'|| = ||r'|| rho
+        proj = abs(r @ rp) / np.linalg.norm(r)
+        assert proj == pytest.approx(np.linalg.norm(rp) * abs(cos), rel=1e-12)
+
+
+def test_zero_residual_drops_penalty():
+    C = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 2.0]])
+    x = np.array([[0.0, 0.0]])                  # x sits on C_0: r = 0
+    for lam in (0.0, 1.0, 5.0):
+        a = oracle.soar_assign(x, C, lam, 1)
+        assert a[0, 0] == 0 and a[0, 1] == 1     # plain second-nearest
+
+
+# ---------------------------------------------------- brute force, tiny data
+
+def test_soar_assign_matches_pure_python_loops():
+    rng = np.random.default_rng(8)
+    n, c, d = 60, 9, 5
+    X = rng.standard_normal((n, d))
+    C = rng.standard_normal((c, d))
+    for lam in (0.0, 1.0, 2.5):
+        got = oracle.soar_assign(X, C, lam, 3)
+        for i in range(n):
+            x = X[i]
+            dist = [sum((x[j] - C[m][j]) ** 2 for j in range(d)) for m in range(c)]
+            a = [min(range(c), key=lambda m: (dist[m], m))]
+            dirs = []
+            for _ in range(3):
+                r = [x[j] - C[a[-1]][j] for j in range(d)]
+                nr = math.sqrt(sum(v * v for v in r))
+                dirs.append([v / nr for v in r] if nr > 0 else [0.0] * d)
+
+                def L(m):
+                    rp = [x[j] - C[m][j] for j in range(d)]
+                    return sum(v * v for v in rp) + lam * sum(
+                        sum(rp[j] * u[j] for j in range(d)) ** 2 for u in dirs)
+
+                cands = [m for m in range(c) if m not in a]
+                a.append(min(cands, key=lambda m: (L(m), m)))
+            assert list(got[i]) == a, (lam, i)
+
+
+def test_primary_assign_matches_cdist_and_ties():
+    rng = np.random.default_rng(9)
+    X = rng.standard_normal((500, 7))
+    C = rng.standard_normal((33, 7))
+    C[20] = C[3]                                 # exact duplicate centroid
+    X[:5] = C[3]                                 # points sitting on it
+    pi, best, gap = oracle.primary_assign(X, C)
+    D = cdist(X, C, "sqeuclidean")
+    np.testing.assert_array_equal(pi, np.argmin(D, axis=1))
+    assert np.all(pi[:5] == 3)                   # tie goes to the lower index
+    assert np.all(gap[:5] == 0)
+    np.testing.assert_allclose(best, D.min(axis=1), atol=1e-10)
+
+
+def test_mips_topk_matches_pure_python_with_ties():
+    rng = np.random.default_rng(10)
+    X = rng.integers(-3, 4, size=(80, 4)).astype(float)   # many exact ties
+    Q = rng.integers(-2, 3, size=(12, 4)).astype(float)
+    ids, sc = oracle.mips_topk(Q, X, 7)
+    for i in range(Q.shape[0]):
+        s = [sum(Q[i][j] * X[m][j] for j in range(4)) for m in range(80)]
+        want = sorted(range(80), key=lambda m: (-s[m], m))[:7]
+        assert list(ids[i]) == want
+        assert list(sc[i]) == [s[m] for m in want]
+
+
+def test_topk_pads_short_lists():
+    ids, sc = oracle.topk_desc(np.array([0.5, 2.0]), 4, np.array([7, 3]))
+    assert list(ids) == [3, 7, -1, -1]
+    assert sc[0] == 2.0 and np.isneginf(sc[2])
+
+
+def test_rank_definition():
+    X = np.array([[1.0, 0.0], [0.0, 1.0], [0.5, 0.5], [1.0, 0.0]])
+    q = np.array([1.0, 0.2])
+    # scores 1.0, 0.2, 0.6, 1.0 -> Rank of X[0] counts both 1.0 entries
+    assert oracle.rank(q, X[0], X) == 2
+    assert oracle.rank(q, X[1], X) == 4
+    assert oracle.rank(q, X[2], X) == 3
+
+
+# ---------------------------------------------------- inverted index, search
+
+def _small_index(seed=12, n=3000, d=16, c=24, lam=1.0, s=1):
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    X /= np.linalg.norm(X, axis=1, keepdims=True)
+    Q = rng.standard_normal((25, d)).astype(np.float32)
+    Q /= np.linalg.norm(Q, axis=1, keepdims=True)
+    C = oracle.kmeans(X, rng.choice(n, c, replace=False), 5)
+    A = oracle.soar_assign(X, C, lam, s)
+    off, ids = oracle.build_ivf(A, c)
+    return X, Q, C, A, off, ids
+
+
+def test_build_ivf_invariants():
+    X, Q, C, A, off, ids = _small_index(s=2)
+    n, c = X.shape[0], C.shape[0]
+    assert off[0] == 0 and off[-1] == n * 3
+    assert np.all(np.diff(off) >= 0)
+    seen = np.zeros((n, c), dtype=int)
+    for p in range(c):
+        mem = ids[off[p]:off[p + 1]]
+        assert np.all(np.diff(mem) > 0)          # ascending, no repeats
+        seen[mem, p] += 1
+    assert np.all(seen.sum(axis=1) == 3)         # exactly 1 + s partitions ...
+    assert np.all(seen.max(axis=1) == 1)         # ... all distinct
+    for i in range(n):
+        assert set(np.nonzero(seen[i])[0]) == set(A[i])
+
+
+def test_search_with_all_partitions_is_brute_force():
+    X, Q, C, A, off, ids = _small_index()
+    got_i, got_s = oracle.ivf_search(Q, X, C, off, ids, 10, C.shape[0])
+    want_i, want_s = oracle.mips_topk(Q, X, 10)
+    np.testing.assert_array_equal(got_i, want_i)
+    np.testing.assert_allclose(got_s, want_s, rtol=1e-12)
+
+
+def test_search_dedups_spilled_copies():
+    X, Q, C, A, off, ids = _small_index()
+    got_i, _ = oracle.ivf_search(Q, X, C, off, ids, 50, 8)
+    for row in got_i:
+        v = row[row >= 0]
+        assert len(v) == len(set(v.tolist()))
+
+
+def test_search_is_topk_of_probed_union():
+    X, Q, C, A, off, ids = _small_index(s=1)
+    t = 5
+    got_i, _ = oracle.ivf_search(Q, X, C, off, ids, 10, t)
+    S = Q.astype(float) @ C.astype(float).T
+    for i in range(Q.shape[0]):
+        parts = sorted(range(C.shape[0]), key=lambda p: (-S[i, p], p))[:t]
+        allowed = [j for j in range(X.shape[0]) if set(A[j]) & set(parts)]
+        s = X[allowed].astype(float) @ Q[i].astype(float)
+        want = [allowed[j] for j in sorted(range(len(allowed)), key=lambda j: (-s[j], allowed[j]))[:10]]
+        assert list(got_i[i]) == want
+
+
+def test_kmr_end_points_and_monotone():
+    X, Q, C, A, off, ids = _small_index()
+    truth, _ = oracle.mips_topk(Q, X, 10)
+    ts = np.arange(0, C.shape[0] + 1)
+    kmr = oracle.kmr_curve(Q, C, A, truth, ts)
+    assert kmr[0] == 0.0 and kmr[-1] == 1.0
+    assert np.all(np.diff(kmr) >= 0)
+    # Eq. 1 written out with the Rank function for one t
+    t = 4
+    hits = 0
+    for i in range(Q.shape[0]):
+        for v in truth[i]:
+            hits += min(oracle.rank(Q[i], C[p], C) for p in A[v]) <= t
+    assert kmr[t] == pytest.approx(hits / (10 * Q.shape[0]))
+
+
+def test_probe_labels_equal_direct_sweep():
+    X, Q, C, A, off, ids = _small_index()
+    truth, _ = oracle.mips_topk(Q, X, 10)
+    lab = oracle.probe_labels(Q, C, A, truth, 0.9)
+    c = C.shape[0]
+    rec = np.stack([oracle.recall_at_k(oracle.ivf_search(Q, X, C, off, ids, 10, t)[0], truth)
+                    for t in range(1, c + 1)])
+    for i in range(Q.shape[0]):
+        first = 1 + int(np.argmax(rec[:, i] >= 0.9 - 1e-12))
+        assert lab[i] == first
+
+
+def test_datapoints_searched_counts_partition_sizes():
+    X, Q, C, A, off, ids = _small_index()
+    ds = oracle.datapoints_searched(Q, C, off, C.shape[0])
+    assert np.all(ds == 2 * X.shape[0])          # every row of a 1-spill index
+    ds1 = oracle.datapoints_searched(Q, C, off, 1)
+    top, _ = oracle.select_partitions(Q, C, 1)
+    np.testing.assert_array_equal(ds1, np.diff(off)[top[:, 0]])
+
+
+def test_recall_helpers():
+    truth = np.array([[1, 2, 3, 4]])
+    found = np.array([[4, 9, 1, -1]])
+    assert oracle.recall_at_k(found, truth)[0] == 0.5
+    X = np.array([[1.0], [0.9], [0.8], [0.7], [0.6], [0.7]])
+    Q = np.array([[1.0]])
+    ids, sc = oracle.mips_topk(Q, X, 4)
+    # id 5 ties id 3 exactly: it counts as a hit under the tie rule
+    assert oracle.recall_at_k_tol(np.array([[0, 1, 2, 5]]), Q, X, sc)[0] == 1.0
+    assert oracle.recall_at_k(np.array([[0, 1, 2, 5]]), ids)[0] == 0.75
+
+
+# ---------------------------------------------------------------- k-means
+
+def test_kmeans_one_step_by_hand():
+    X = np.array([[0.0], [1.0], [2.0], [10.0], [11.0]], dtype=np.float32)
+    C = oracle.kmeans(X, np.array([0, 3]), 1)
+    np.testing.assert_allclose(C[:, 0], [1.0, 10.5])
+    C2 = oracle.kmeans(X, np.array([0, 1]), 2)
+    # step 1: {0} {1,2,10,11} -> 0, 6 ; step 2: {0,1,2} {10,11} -> 1, 10.5
+    np.testing.assert_allclose(C2[:, 0], [1.0, 10.5])
+
+
+def test_kmeans_empty_cluster_keeps_centroid():
+    X = np.array([[0.0], [0.1], [0.2]], dtype=np.float32)
+    init = np.array([0, 1])
+    X2 = np.concatenate([X, np.array([[50.0]], dtype=np.float32)])
+    C = oracle.kmeans(X2, np.array([0, 3]), 1)
+    assert C[1, 0] == 50.0
+    # a centroid that attracts nothing stays where it is
+    X3 = np.array([[0.0], [0.0], [0.1]], dtype=np.float32)
+    C3 = oracle.kmeans(X3, np.array([0, 1]), 1)   # both seeds at 0: tie -> all to index 0
+    assert C3[1, 0] == 0.0
+    assert C3[0, 0] == pytest.approx(np.float32(0.1 / 3))
+    del init
+
+
+def test_kmeans_objective_non_increasing():
+    rng = np.random.default_rng(13)
+    X = rng.standard_normal((2000, 8)).astype(np.float32)
+    _, hist = oracle.kmeans(X, rng.choice(2000, 30, replace=False), 8, return_history=True)
+    assert all(b <= a + 1e-9 for a, b in zip(hist, hist[1:]))
+
+
+# --------------------------------------------- low precision and the MLP
+
+def test_fp8_round_matches_torch():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(14)
+    v = np.concatenate([rng.uniform(-448, 448, 20000), rng.uniform(-1, 1, 20000) * 2.0 ** -6,
+                        np.array([0.0, 448.0, -448.0, 2.0 ** -9, 2.0 ** -10, 1.0625, 1.1875])])
+    v = v.astype(np.float32)
+    want = torch.from_numpy(v).to(torch.float8_e4m3fn).to(torch.float32).numpy()
+    np.testing.assert_array_equal(oracle.fp8_e4m3_round(v), want)
+
+
+def test_fp8_saturates_and_scales():
+    assert oracle.fp8_e4m3_round(np.array([470.0, -1e6]))[0] == 448.0
+    codes, scale = oracle.quantize_rows_fp8(np.array([[0.5, -2.0, 1.0], [0, 0, 0]], dtype=np.float32))
+    assert scale[0] == np.float32(2.0) / np.float32(448.0) and scale[1] == 1.0
+    assert codes[0, 1] == -448.0
+
+
+def test_bf16_round_matches_torch():
+    torch = pytest.importorskip("torch")
+    v = np.random.default_rng(15).standard_normal(50000).astype(np.float32)
+    want = torch.from_numpy(v).to(torch.bfloat16).to(torch.float32).numpy()
+    np.testing.assert_array_equal(oracle.bf16_round(v), want)
+
+
+def test_precision_search_exhaustive_rescore_is_exact():
+    X, Q, C, A, off, ids = _small_index()
+    Xb, Qb = oracle.bf16_round(X), oracle.bf16_round(Q)
+    got_i, _ = oracle.precision_search(Qb, Xb, C, off, ids, 10, C.shape[0], X.shape[0])
+    want_i, _ = oracle.mips_topk(Qb, Xb, 10)
+    np.testing.assert_array_equal(got_i, want_i)
+
+
+def test_mlp_gradients_match_finite_differences():
+    rng = np.random.default_rng(16)
+    p = probe_mlp.init_params(9, 6, 1)
+    for name in ("b1", "b2", "b3"):
+        p[name] = rng.standard_normal(p[name].shape) * 0.1
+    Z = rng.standard_normal((13, 9))
+    y = rng.standard_normal(13)
+    g = probe_mlp.backward(p, Z, y)
+    eps = 1e-6
+    for name in probe_mlp.PARAM_NAMES:
+        flat = p[name].reshape(-1)
+        for j in range(0, flat.size, max(1, flat.size // 7)):
+            old = flat[j]
+            flat[j] = old + eps
+            lp = probe_mlp.loss(p, Z, y)
+            flat[j] = old - eps
+            lm = probe_mlp.loss(p, Z, y)
+            flat[j] = old
+            assert g[name].reshape(-1)[j] == pytest.approx((lp - lm) / (2 * eps), rel=1e-5, abs=1e-8)
+
+
+def test_mlp_adam_matches_hand_update():
+    p = {"W1": np.array([[1.0]]), "b1": np.zeros(1), "W2": np.array([[1.0]]), "b2": np.zeros(1),
+         "W3": np.array([[1.0]]), "b3": np.zeros(1)}
+    g = {k: np.ones_like(v) for k, v in p.items()}
+    m = {k: np.zeros_like(v) for k, v in p.items()}
+    v = {k: np.zeros_like(v) for k, v in p.items()}
+    probe_mlp.adam_step(p, g, m, v, 1, 0.1)
+    # first Adam step moves each parameter by lr * sign(g) (bias corrected)
+    assert p["W1"][0, 0] == pytest.approx(1.0 - 0.1, rel=1e-6)
