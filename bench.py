@@ -1,0 +1,463 @@
+#!/usr/bin/env python
+"""QPS at recall@10 >= 0.9 of the SOAR spilled-IVF index on one GB300.
+
+Workload (default ``glove``): n = 1,183,514 unit vectors, d = 100, drawn from
+a seeded 500-component anisotropic Gaussian mixture; c = 2000 partitions by
+10 Lloyd iterations; SOAR lambda = 1 with one spill; 10,000 queries from the
+same mixture; top-10 maximum inner product.
+
+Setup (untimed): synthetic data, GPU k-means, assignment and index build for
+three arms (SOAR lambda=1 s=1, spilled without SOAR lambda=0 s=1, no spill),
+exact ground truth by GPU brute force, and per arm the smallest probe count
+t with mean recall@10 >= 0.9.
+
+A step is one soar_search of the whole 10,000-query batch at the SOAR arm's
+t, inputs resident in HBM; L2 is flushed (256 MB write) between steps and the
+step is timed with CUDA events on the search stream.  `e2e` repeats the step
+through the same public call with the queries copied from pinned host
+memory and the results copied back inside the timed region.
+
+With ``--impl reference`` the CPU oracle (``oracle/``) is timed instead on a
+bounded sample of queries over its own index.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS, FALLBACK_BF16_TFLOPS = 6800.0, 1900.0
+SMS, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
+METRIC = "QPS at recall@10>=0.9"
+RECALL_TARGET = 0.9
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default="glove", choices=["glove", "tiny"])
+    p.add_argument("--nq", type=int, default=None, help="queries per step per GPU")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-sample", type=int, default=300, help="queries timed on the CPU oracle")
+    return p.parse_args()
+
+
+def peaks():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            m = json.load(f)
+        return float(m["hbm_gbs"]), float(m["bf16_tflops"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, FALLBACK_BF16_TFLOPS, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+
+def recall_at_k(ids, truth):
+    import torch
+    hit = (ids[:, :, None] == truth[:, None, :]).any(dim=2)
+    return hit.float().sum(dim=1) / truth.shape[1]
+
+
+def datapoints_searched(sb, index, Qd, t, offsets):
+    import torch
+    top = sb.soar_select_partitions(index, Qd, t).long()
+    sizes = (offsets[1:] - offsets[:-1])
+    return sizes[top].sum(dim=1), top
+
+
+def find_t(sb, index, Qd, truth, k, t_max):
+    """Smallest t in [1, t_max] with mean recall@k >= target (recall is monotone in t)."""
+    def rec(t):
+        ids, _ = sb.soar_search(index, Qd, k, t)
+        return float(recall_at_k(ids, truth).mean())
+    lo, hi = 1, t_max
+    if rec(hi) < RECALL_TARGET:
+        return None, rec(hi)
+    while lo < hi:
+        mid = (lo + hi) // 2
+        if rec(mid) >= RECALL_TARGET:
+            hi = mid
+        else:
+            lo = mid + 1
+    return lo, rec(lo)
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_2404_00774_gb300", "csrc", "search.cu"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload):
+    """Per-launch DRAM bytes of the scan kernel from a committed ncu summary,
+    if that summary was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", f"scan_kernel_{workload}.txt")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    mh = re.search(r"source_hash:\s*(\w+)", txt)
+    mb = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not mh or not mb or mh.group(1) != kernel_hash():
+        return None
+    return float(mb.group(1))
+
+
+# ------------------------------------------------------------------ oracle
+
+def oracle_index(X, w, lam, spills, train_rows=50_000, iters=10):
+    """The oracle's own index over the same data (codebook trained on a prefix of X)."""
+    import oracle
+    init = synth.init_indices(min(train_rows, X.shape[0]), w.c, w.init_seed)
+    C = oracle.kmeans(X[:train_rows], init, iters)
+    A = oracle.soar_assign(X, C, lam, spills)
+    off, ids = oracle.build_ivf(A, w.c)
+    return C, off, ids
+
+
+def time_oracle(X, Q, C, off, ids, k, t, sample):
+    import oracle
+    Qs = Q[:sample]
+    t0 = time.perf_counter()
+    oracle.ivf_search(Qs, X, C, off, ids, k, t)
+    dt = time.perf_counter() - t0
+    return sample / dt, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = synth.WORKLOADS[args.workload]
+    X, Q, _ = synth.workload_arrays(args.workload, nq=max(args.cpu_sample, 64))
+    t0 = time.perf_counter()
+    C, off, ids = oracle_index(X, w, w.lam, w.spills)
+    setup = time.perf_counter() - t0
+    import oracle
+    truth, _ = oracle.mips_topk(Q[:64], X, w.k)
+    # smallest t reaching the recall target on the oracle's own index
+    t = 1
+    while t < w.c:
+        got, _ = oracle.ivf_search(Q[:64], X, C, off, ids, w.k, t)
+        if oracle.recall_at_k(got, truth).mean() >= RECALL_TARGET:
+            break
+        t = min(w.c, t * 2)
+    per_step = max(8, args.cpu_sample // max(1, args.steps))
+    for i in range(args.warmup):
+        oracle.ivf_search(Q[:per_step], X, C, off, ids, w.k, t)
+    times = []
+    for i in range(args.steps):
+        lo = (i * per_step) % max(1, Q.shape[0] - per_step)
+        t1 = time.perf_counter()
+        oracle.ivf_search(Q[lo:lo + per_step], X, C, off, ids, w.k, t)
+        times.append(time.perf_counter() - t1)
+    qps = per_step * len(times) / sum(times)
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload} n={w.n} d={w.d} c={w.c} lambda={w.lam} spills={w.spills} k={w.k}",
+                   "t": t, "queries_per_step": per_step, "index": "oracle's own (k-means on 50k rows)"},
+        "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} queries per step x {args.steps} steps, t={t}",
+                         "setup_s": setup},
+        "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_ours(args):
+    import torch
+    from paper_2404_00774_gb300 import binding as sb
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    sb.load()
+    dev = torch.device("cuda", local)
+    w = synth.WORKLOADS[args.workload]
+    nq = args.nq or w.nq
+    k = w.k
+
+    t0 = time.perf_counter()
+    mix = synth.mixture_for(w)
+    X = mix.sample(w.n, w.data_seed)
+    Qall = mix.sample(nq * world, w.query_seed)
+    Q = Qall[rank * nq:(rank + 1) * nq]          # queries are sharded across ranks
+    init = synth.init_indices(w.n, w.c, w.init_seed)
+    log(f"[bench] data {time.perf_counter() - t0:.1f}s")
+    Xd = torch.from_numpy(X).to(dev)
+    Qd = torch.from_numpy(Q).to(dev)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        out = fn()
+        b.record(stream)
+        b.synchronize()
+        return out, a.elapsed_time(b)
+
+    # ---- build (untimed for the metric; reported as build throughput)
+    C, km_ms = timed(lambda: sb.soar_train_centroids(Xd, w.c, w.kmeans_iters, torch.from_numpy(init).to(dev)))
+    arms = {"soar": (w.lam, w.spills), "spill_no_soar": (0.0, w.spills), "no_spill": (0.0, 0)}
+    built = {}
+    assign_ms = {}
+    for name, (lam, s) in arms.items():
+        A, ms = timed(lambda: sb.soar_assign(Xd, C, lam, s))
+        assign_ms[name] = ms
+        ix, bms = timed(lambda: sb.soar_index_build(Xd, C, A))
+        built[name] = (ix, bms)
+        del A
+    truth, gt_ms = timed(lambda: sb.soar_exact_mips(Xd, Qd, k)[0])
+    log(f"[bench] kmeans {km_ms:.1f} ms, assign {assign_ms}, truth {gt_ms:.1f} ms")
+
+    results = {}
+    for name, (ix, bms) in built.items():
+        t, rec = find_t(sb, ix, Qd, truth, k, min(w.c, 512))
+        offsets = ix.offsets()
+        ds = float(datapoints_searched(sb, ix, Qd, t, offsets)[0].float().mean()) if t else None
+        results[name] = {"t": t, "recall": rec, "datapoints_searched": ds, "build_ms": bms,
+                         "assign_ms": assign_ms[name], "index_bytes": int(ix.info.device_bytes)}
+        log(f"[bench] {name}: t={t} recall={rec:.4f} datapoints={ds}")
+
+    ix = built["soar"][0]
+    t_main = results["soar"]["t"]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+
+    def step_times(index, t, steps, warmup, stage=False):
+        for _ in range(warmup):
+            sb.soar_search(index, Qd, k, t)
+        torch.cuda.synchronize()
+        if stage:
+            sb.soar_stage_times()
+            sb.soar_stage_timing(True)
+        ts = []
+        for i in range(steps):
+            flush.fill_(float(i))
+            (_, ms) = timed(lambda: sb.soar_search(index, Qd, k, t))
+            ts.append(ms)
+        if stage:
+            sb.soar_stage_timing(False)
+        return ts
+
+    # ---- other arms, a few steps each (context for the metric)
+    for name in ("spill_no_soar", "no_spill"):
+        tt = results[name]["t"]
+        if tt:
+            ms = statistics.mean(step_times(built[name][0], tt, 5, 2))
+            results[name]["qps"] = nq / (ms / 1e3)
+
+    # ---- the timed region
+    for _ in range(args.warmup):
+        sb.soar_search(ix, Qd, k, t_main)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sb.soar_stage_times()
+    launches0 = sb.soar_kernel_launches()
+    with ClockSampler(local) as clocks:
+        sb.soar_stage_timing(True)
+        ts = []
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            (_, ms) = timed(lambda: sb.soar_search(ix, Qd, k, t_main))
+            ts.append(ms)
+        sb.soar_stage_timing(False)
+        torch.cuda.synchronize()
+    launches = sb.soar_kernel_launches() - launches0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    stages = sb.soar_stage_times()
+    ms_step = statistics.mean(ts)
+    if dist:
+        tt = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_step = float(tt)
+    results["soar"]["qps"] = nq / (ms_step / 1e3)
+
+    # ---- e2e: pinned host queries in, results out, through the same call
+    Qh = torch.from_numpy(Q).pin_memory()
+    ids_h = torch.empty((nq, k), dtype=torch.int64).pin_memory()
+    sc_h = torch.empty((nq, k), dtype=torch.float32).pin_memory()
+    Qdev = torch.empty_like(Qd)
+
+    def e2e_once():
+        Qdev.copy_(Qh, non_blocking=True)
+        ids, sc = sb.soar_search(ix, Qdev, k, t_main)
+        ids_h.copy_(ids, non_blocking=True)
+        sc_h.copy_(sc, non_blocking=True)
+
+    for _ in range(2):
+        e2e_once()
+    e2e_ts = []
+    for i in range(max(3, args.steps // 2)):
+        flush.fill_(float(i))
+        (_, ms) = timed(e2e_once)
+        e2e_ts.append(ms)
+    e2e_ms = statistics.mean(e2e_ts)
+
+    # ---- roofline of the dominant kernel (the partition scan)
+    hbm, bf16, peak_src = peaks()
+    scan_ms, scan_n = stages.get("scan", (float("nan"), 1))
+    scan_ms_per = scan_ms / max(1, scan_n)
+    offsets = ix.offsets()
+    dsq, top = datapoints_searched(sb, ix, Qd, t_main, offsets)
+    pairs_rows = float(dsq.sum())                      # (query, row) pairs scored per launch
+    flops = 2.0 * w.d * pairs_rows
+    probed = torch.unique(top)
+    sizes = (offsets[1:] - offsets[:-1])
+    rows_read = float(sizes[probed].sum())
+    row_bytes = ix.info.row_stride * 4 + 4
+    bytes_alg = rows_read * row_bytes + nq * ix.info.row_stride * 4 + nq * t_main * k * 8
+    alu_peak = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12     # TFLOP/s
+    tflops = flops / (scan_ms_per / 1e3) / 1e12
+    gbs = bytes_alg / (scan_ms_per / 1e3) / 1e9
+    if tflops / alu_peak >= gbs / hbm:
+        roof = {"bound": "alu", "achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": tflops / alu_peak, "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
+    else:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                "peak_source": f"{peak_src} hbm_gbs"}
+    traffic = profiled_traffic(args.workload)
+    roof.update({"traffic": traffic, "kernel": "scan_kernel", "ms_per_launch": scan_ms_per,
+                 "algorithmic_bytes": bytes_alg, "algorithmic_flops": flops,
+                 "hbm_gbs_achieved": gbs, "hbm_frac": gbs / hbm, "alu_tflops_achieved": tflops})
+
+    # ---- CPU oracle baseline (rank 0 only, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t1 = time.perf_counter()
+        Co, offo, idso = oracle_index(X, w, w.lam, w.spills)
+        setup = time.perf_counter() - t1
+        qps_cpu, secs = time_oracle(X, Q, Co, offo, idso, k, t_main, args.cpu_sample)
+        cpu = {"value": qps_cpu, "unit": "queries/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{args.cpu_sample} queries at t={t_main} over the oracle's own index "
+                         f"(fp64 numpy, {secs:.1f} s)", "setup_s": setup}
+
+    total_q = nq * world
+    line = {
+        "metric": METRIC, "value": total_q / (ms_step / 1e3), "unit": "queries/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: n={w.n} d={w.d} c={w.c} lambda={w.lam} spills={w.spills} "
+                               f"nq={nq}/gpu k={k}", "t": t_main, "recall@10": results["soar"]["recall"],
+                   "l2": "flushed between steps (256 MB write)", "index": "replicated per GPU",
+                   "parallelism": f"queries sharded over {world} GPU(s)"},
+        "e2e": {"value": total_q / (e2e_ms / 1e3), "unit": "queries/s", "h2d_bytes_per_step": int(Q.nbytes),
+                "d2h_bytes_per_step": int(nq * k * 12)},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clocks.summary(),
+        "arms": results,
+        "build": {"kmeans_ms": km_ms, "assign_ms": assign_ms["soar"],
+                  "assignments_per_s": w.n / (assign_ms["soar"] / 1e3), "ground_truth_ms": gt_ms},
+        "stages_ms_per_step": {s: v[0] / max(1, v[1]) for s, v in stages.items()},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for ixx, _ in built.values():
+        ixx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,231 @@
+/*
+ * soar.h -- C ABI of the GB300 (sm_103a) SOAR spilled-IVF library.
+ *
+ * SOAR ("Spilling with Orthogonality-Amplified Residuals", Sun et al.,
+ * arXiv 2404.00774) builds an inverted-file (IVF) index over a codebook C
+ * of c centroids and assigns every datapoint x to its nearest centroid
+ * pi(x) plus `spills` further centroids chosen by the loss of Theorem 3.1,
+ *     ||x - c'||^2 + lambda * <x - c', r_hat>^2,   r_hat = (x - C[pi(x)]) / ||x - C[pi(x)]||.
+ * Search (Section 2.2) ranks the centroids by <q, C_i>, scans the top t
+ * partitions, removes the duplicate copies that spilling creates
+ * (Section 3.5) and returns the top k by <q, x> (maximum inner product,
+ * Section 2.1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Array arguments are DEVICE pointers owned by the caller unless a
+ *   comment says "host".  Matrices are dense row-major; a vector set
+ *   X[n][d] has row stride d elements.  Rows must be 4-byte aligned;
+ *   16-byte aligned rows (d*elem_size a multiple of 16) take faster loads.
+ * - `stream` orders the call's device work; calls return as soon as the
+ *   work is queued unless documented otherwise.  The caller synchronises.
+ *   Scratch memory is taken from the device's stream-ordered pool
+ *   (cudaMallocAsync on `stream`) and released in stream order.
+ * - Every call returns a soar_status and never throws across the ABI.
+ *   Argument errors return SOAR_EINVAL before any device work is queued
+ *   and leave outputs untouched.  soar_last_error() gives a thread-local
+ *   message for the last failing call on the calling thread.
+ * - Tie rules: an argmin over centroids prefers the lower centroid index;
+ *   top-t partitions and top-k results are ordered by score descending,
+ *   the lower id first on equal scores.  Fewer than k distinct candidates
+ *   leave id -1 and score -inf in the tail.
+ * - Errors raised by kernels after the call returned surface at the next
+ *   synchronising CUDA call as SOAR_ECUDA.
+ */
+#ifndef SOAR_H
+#define SOAR_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#if defined(__GNUC__)
+#define SOAR_API __attribute__((visibility("default")))
+#else
+#define SOAR_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SOAR_OK = 0,
+  SOAR_EINVAL = 1,        /* invalid argument (sizes, null pointers, NaN lambda ...) */
+  SOAR_ENOMEM = 2,        /* device allocation failed */
+  SOAR_ECUDA = 3,         /* a CUDA runtime error (message in soar_last_error) */
+  SOAR_ETIMEOUT = 4,      /* a bounded device wait ran out */
+  SOAR_EUNSUPPORTED = 5   /* valid but outside what this build implements */
+} soar_status;
+
+/* Element type of caller-provided vector sets (datapoints, queries). */
+typedef enum { SOAR_F32 = 0, SOAR_BF16 = 1 } soar_dtype;
+
+/* How an index scores candidates during search.
+ * SOAR_SCORE_F32: duplicated rows are stored in the input dtype and scored
+ *   exactly (fp32 products and sums).
+ * SOAR_SCORE_FP8: duplicated rows are FP8-E4M3 codes with one fp32 scale
+ *   per row (scale = max|row| / 448); queries and centroids are scored the
+ *   same way; a single copy of the original vectors, indexed by id, serves
+ *   the exact fp32 rescoring of the best `rescore` candidates.  This is the
+ *   GPU analogue of the paper's layout in Section 3.5: only the compressed
+ *   representation is duplicated, the highest-bitrate copy is stored once.
+ */
+typedef enum { SOAR_SCORE_F32 = 0, SOAR_SCORE_BF16 = 1, SOAR_SCORE_FP8 = 2 } soar_score_mode;
+
+typedef struct soar_index soar_index;   /* opaque; owns its device memory */
+
+/* Thread-local message of the last failing call ("" if none). */
+SOAR_API const char* soar_last_error(void);
+
+/* Library version string, e.g. "soar-gb300 0.1 sm_103a". */
+SOAR_API const char* soar_version(void);
+
+/*
+ * Lloyd k-means (Section 2.2: "Vector quantization" trains the codebook C).
+ *   X        [n][d] datapoints (dtype)
+ *   init_idx [c]    distinct row indices of X used as the initial centroids
+ *                   (the caller draws them; the library draws no random numbers)
+ *   C_out    [c][d] fp32 output codebook
+ * Each of `iters` iterations assigns every point to its nearest centroid
+ * (ties to the lower index) and replaces every non-empty centroid by the
+ * mean of its points, summed in fp64 and rounded to fp32; an empty cluster
+ * keeps its previous centroid.  Requires 1 <= c <= n, iters >= 0, d >= 1;
+ * init_idx entries outside [0, n) give SOAR_EINVAL (checked on the device,
+ * which costs one synchronisation of `stream`).
+ */
+SOAR_API soar_status soar_train_centroids(const void* X, soar_dtype dtype, int64_t n, int32_t d,
+                                 int32_t c, int32_t iters, const int32_t* init_idx,
+                                 float* C_out, cudaStream_t stream);
+
+/*
+ * Primary and SOAR spilled assignment (Section 2.2 for pi; Eq. 2 and
+ * Theorem 3.1 for the spills; Section 3.5 for the order of the pipeline).
+ *   X          [n][d] datapoints (dtype)
+ *   C          [c][d] fp32 codebook
+ *   assign_out [n][1 + spills] int32: column 0 is pi(x) = argmin ||x - C_i||^2,
+ *              column j >= 1 is the j-th spilled partition, the argmin over
+ *              centroids not yet assigned to x of
+ *                  ||x - c'||^2 + lambda * sum_{i<j} <x - c', r_hat_i>^2,
+ *              r_hat_i the unit residual of the i-th earlier assignment
+ *              (j = 1 is exactly the paper's loss; a zero residual adds no
+ *              penalty).  lambda = 0 gives plain nearest-centroid spilling.
+ * Requires lambda finite and >= 0, 0 <= spills <= 4, c >= 1 + spills.
+ */
+SOAR_API soar_status soar_assign(const void* X, soar_dtype dtype, int64_t n, int32_t d,
+                        const float* C, int32_t c, float lambda, int32_t spills,
+                        int32_t* assign_out, cudaStream_t stream);
+
+/*
+ * Inverted-file index over a codebook and an assignment (Section 2.2,
+ * Section 3.5).  Partition p lists, in ascending id, every point with p in
+ * its assignment row; each listed point's vector is copied next to its id
+ * so a partition is one contiguous block of rows.
+ *   X      [n][d] datapoints (dtype); copied, the caller may free it after the call
+ *   C      [c][d] fp32 codebook; copied
+ *   assign [n][1 + spills] int32 (as produced by soar_assign)
+ *   out    host pointer that receives the new index handle
+ * This call synchronises `stream` once (to size the index) and returns
+ * after the index is complete.  Every assignment must lie in [0, c) and the
+ * entries of a row must be distinct (checked; SOAR_EINVAL otherwise).
+ */
+SOAR_API soar_status soar_index_build(const void* X, soar_dtype dtype, int64_t n, int32_t d,
+                             const float* C, int32_t c, const int32_t* assign, int32_t spills,
+                             soar_score_mode mode, soar_index** out, cudaStream_t stream);
+
+/* Read-only description of an index (all pointers are device pointers owned by the index). */
+typedef struct {
+  int64_t n;               /* datapoints */
+  int32_t d;               /* dimension */
+  int32_t c;               /* partitions */
+  int32_t spills;          /* extra assignments per point */
+  int32_t mode;            /* soar_score_mode */
+  int32_t dtype;           /* soar_dtype of the stored vectors */
+  int32_t row_stride;      /* elements per stored row (>= d, padded for 16-byte rows) */
+  int64_t rows;            /* n * (1 + spills) */
+  int64_t max_partition;   /* largest partition size */
+  const int64_t* offsets;  /* [c + 1] partition p is rows offsets[p] .. offsets[p+1]-1 */
+  const int32_t* ids;      /* [rows] point id of each row */
+  const void* vectors;     /* [rows][row_stride] dtype (SOAR_SCORE_F32) or FP8 codes (SOAR_SCORE_FP8) */
+  const float* row_scales; /* [rows] per-row FP8 scale (SOAR_SCORE_FP8) or NULL */
+  const void* originals;   /* [n][row_stride] single copy for rescoring (SOAR_SCORE_FP8) or NULL */
+  const float* centroids;  /* [c][d] fp32 */
+  int64_t device_bytes;    /* device memory held by the index */
+} soar_index_info;
+
+SOAR_API soar_status soar_index_get_info(const soar_index* index, soar_index_info* info /* host */);
+
+/* Frees the index and its device memory (after synchronising the device work that used it). */
+SOAR_API soar_status soar_index_free(soar_index* index);
+
+/*
+ * Top-t partitions per query: MIPS_t(q, C) (Section 2.2), the centroids of
+ * largest <q, C_i>, in rank order.
+ *   Q         [nq][d] queries (dtype)
+ *   top_out   [nq][t] int32 partition ids
+ *   score_out [nq][t] fp32 scores, may be NULL
+ * Scores are fp32 (SOAR_SCORE_F32 indices) or FP8-scaled (SOAR_SCORE_FP8).
+ * Requires 1 <= t <= min(c, 8192).
+ */
+SOAR_API soar_status soar_select_partitions(const soar_index* index, const void* Q, soar_dtype dtype,
+                                   int64_t nq, int32_t t, int32_t* top_out, float* score_out,
+                                   cudaStream_t stream);
+
+/*
+ * IVF search with deduplication of spilled copies (Section 2.2, Section 3.5).
+ *   Q           [nq][d] queries (dtype)
+ *   t           partitions probed per query (1 <= t <= min(c, 8192))
+ *   t_per_query [nq] int32 per-query probe counts in [1, t], or NULL for t everywhere
+ *   rescore     SOAR_SCORE_FP8 indices: candidates kept per query for exact fp32
+ *               rescoring (k <= rescore <= 4096); ignored (pass 0) for SOAR_SCORE_F32
+ *   ids_out     [nq][k] int64 point ids, scores_out [nq][k] fp32 <q, x>
+ * Requires 1 <= k <= 1024.
+ */
+SOAR_API soar_status soar_search(const soar_index* index, const void* Q, soar_dtype dtype, int64_t nq,
+                        int32_t k, int32_t t, const int32_t* t_per_query, int32_t rescore,
+                        int64_t* ids_out, float* scores_out, cudaStream_t stream);
+
+/*
+ * Exact maximum inner product search MIPS_k(q, X) (Section 2.1) by brute
+ * force: fp32 products and sums over every datapoint.
+ *   X [n][d] (xdtype), Q [nq][d] (qdtype), ids_out [nq][k] int64, scores_out [nq][k] fp32.
+ * Requires 1 <= k <= 1024.
+ */
+SOAR_API soar_status soar_exact_mips(const void* X, soar_dtype xdtype, int64_t n, int32_t d,
+                            const void* Q, soar_dtype qdtype, int64_t nq, int32_t k,
+                            int64_t* ids_out, float* scores_out, cudaStream_t stream);
+
+/*
+ * Per-row FP8-E4M3 quantisation used by SOAR_SCORE_FP8 indices:
+ * scale[i] = max_j |V[i][j]| / 448 (1 when the row is zero) and
+ * codes[i][j] = e4m3(V[i][j] / scale[i]) rounded to nearest-even and
+ * saturated to +-448.  Exposed so the codes can be checked bit for bit.
+ *   V [m][d] (dtype), codes [m][code_stride] uint8 (code_stride >= d), scales [m] fp32.
+ */
+SOAR_API soar_status soar_quantize_fp8(const void* V, soar_dtype dtype, int64_t m, int32_t d,
+                              uint8_t* codes, int32_t code_stride, float* scales,
+                              cudaStream_t stream);
+
+/* ------------------------------------------------------------------ *
+ * Instrumentation (measurement support; not part of the paper's method)
+ * ------------------------------------------------------------------ */
+
+/* Number of CUDA kernels this library has launched in this process. */
+SOAR_API uint64_t soar_kernel_launches(void);
+
+/* Turns on (1) or off (0) CUDA-event timing of the named stages of
+ * soar_search ("select", "group", "scan", "merge", "rescore"); events are
+ * recorded on the call's stream around each stage, adding no synchronisation. */
+SOAR_API soar_status soar_stage_timing(int enable);
+
+/* Waits for the recorded events, writes the total milliseconds and the
+ * number of timed launches per stage since the last read, and clears them.
+ * `names` (host, names_len bytes) receives the comma-separated stage names
+ * in the order of `ms` / `launches` (host arrays of max_stages entries).
+ * Returns the number of stages written. */
+SOAR_API int soar_stage_times(char* names, int names_len, float* ms, int* launches, int max_stages);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SOAR_H */

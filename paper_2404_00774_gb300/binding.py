@@ -1,0 +1,275 @@
+"""Thin Python binding of libsoar.so (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of its own: it checks shapes and dtypes of torch CUDA tensors,
+passes their device pointers and the current CUDA stream, and raises
+``SoarError`` on a non-zero status.  There is no CPU fallback: if the shared
+library is missing, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsoar.so")
+
+SOAR_OK, SOAR_EINVAL, SOAR_ENOMEM, SOAR_ECUDA, SOAR_ETIMEOUT, SOAR_EUNSUPPORTED = range(6)
+SOAR_F32, SOAR_BF16 = 0, 1
+SOAR_SCORE_F32, SOAR_SCORE_BF16, SOAR_SCORE_FP8 = 0, 1, 2
+STATUS_NAMES = {0: "SOAR_OK", 1: "SOAR_EINVAL", 2: "SOAR_ENOMEM", 3: "SOAR_ECUDA",
+                4: "SOAR_ETIMEOUT", 5: "SOAR_EUNSUPPORTED"}
+
+_lib = None
+
+
+class SoarError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class IndexInfo(ct.Structure):
+    _fields_ = [("n", ct.c_int64), ("d", ct.c_int32), ("c", ct.c_int32), ("spills", ct.c_int32),
+                ("mode", ct.c_int32), ("dtype", ct.c_int32), ("row_stride", ct.c_int32),
+                ("rows", ct.c_int64), ("max_partition", ct.c_int64), ("offsets", ct.c_void_p),
+                ("ids", ct.c_void_p), ("vectors", ct.c_void_p), ("row_scales", ct.c_void_p),
+                ("originals", ct.c_void_p), ("centroids", ct.c_void_p), ("device_bytes", ct.c_int64)]
+
+
+_P, _I32, _I64, _F32 = ct.c_void_p, ct.c_int32, ct.c_int64, ct.c_float
+_SIGS = {
+    "soar_last_error": ([], ct.c_char_p),
+    "soar_version": ([], ct.c_char_p),
+    "soar_train_centroids": ([_P, _I32, _I64, _I32, _I32, _I32, _P, _P, _P], _I32),
+    "soar_assign": ([_P, _I32, _I64, _I32, _P, _I32, _F32, _I32, _P, _P], _I32),
+    "soar_index_build": ([_P, _I32, _I64, _I32, _P, _I32, _P, _I32, _I32, ct.POINTER(_P), _P], _I32),
+    "soar_index_get_info": ([_P, ct.POINTER(IndexInfo)], _I32),
+    "soar_index_free": ([_P], _I32),
+    "soar_select_partitions": ([_P, _P, _I32, _I64, _I32, _P, _P, _P], _I32),
+    "soar_search": ([_P, _P, _I32, _I64, _I32, _I32, _P, _I32, _P, _P, _P], _I32),
+    "soar_exact_mips": ([_P, _I32, _I64, _I32, _P, _I32, _I64, _I32, _P, _P, _P], _I32),
+    "soar_quantize_fp8": ([_P, _I32, _I64, _I32, _P, _I32, _P, _P], _I32),
+    "soar_kernel_launches": ([], ct.c_uint64),
+    "soar_stage_timing": ([_I32], _I32),
+    "soar_stage_times": ([ct.c_char_p, _I32, _P, _P, _I32], _I32),
+}
+
+
+def load():
+    """Loads libsoar.so (built by ``paper_2404_00774_gb300.build``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2404_00774_gb300.build`"
+                           " (there is no CPU fallback)")
+    lib = ct.CDLL(LIB_PATH)
+    for name, (args, res) in _SIGS.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != SOAR_OK:
+        raise SoarError(status, load().soar_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ct.c_void_p(stream.cuda_stream)
+
+
+def _dtype(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return SOAR_F32
+    if t.dtype == torch.bfloat16:
+        return SOAR_BF16
+    raise TypeError(f"vectors must be float32 or bfloat16, got {t.dtype}")
+
+
+def _dev(t: torch.Tensor, name: str, dtype=None, ndim=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if ndim is not None and t.dim() != ndim:
+        raise ValueError(f"{name} must have {ndim} dimensions")
+    return ct.c_void_p(t.data_ptr())
+
+
+def version() -> str:
+    return load().soar_version().decode()
+
+
+def soar_train_centroids(X: torch.Tensor, c: int, iters: int, init_idx: torch.Tensor, out=None, stream=None):
+    n, d = X.shape
+    if out is None:
+        out = torch.empty((c, d), dtype=torch.float32, device=X.device)
+    _check(load().soar_train_centroids(_dev(X, "X", ndim=2), _dtype(X), n, d, c, iters,
+                                       _dev(init_idx, "init_idx", torch.int32, 1),
+                                       _dev(out, "out", torch.float32, 2), _stream(stream)))
+    return out
+
+
+def soar_assign(X: torch.Tensor, C: torch.Tensor, lam: float, spills: int, out=None, stream=None):
+    n, d = X.shape
+    c = C.shape[0]
+    if C.shape[1] != d:
+        raise ValueError("C and X disagree on d")
+    if out is None:
+        out = torch.empty((n, 1 + spills), dtype=torch.int32, device=X.device)
+    _check(load().soar_assign(_dev(X, "X", ndim=2), _dtype(X), n, d, _dev(C, "C", torch.float32, 2), c,
+                              float(lam), spills, _dev(out, "out", torch.int32, 2), _stream(stream)))
+    return out
+
+
+class Index:
+    """Owner of a soar_index handle (freed on ``close`` or garbage collection)."""
+
+    def __init__(self, handle: ct.c_void_p):
+        self._h = handle
+        self.info = IndexInfo()
+        _check(load().soar_index_get_info(self._h, ct.byref(self.info)))
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("index is closed")
+        return self._h
+
+    def close(self):
+        if self._h is not None:
+            _check(load().soar_index_free(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # device arrays owned by the index, as torch views
+    def _view(self, ptr, count, dtype):
+        if count == 0:
+            return torch.empty(0, dtype=dtype, device="cuda")
+        return _wrap_device(ptr, count, dtype)
+
+    def offsets(self) -> torch.Tensor:
+        return self._view(self.info.offsets, self.info.c + 1, torch.int64).clone()
+
+    def ids(self) -> torch.Tensor:
+        return self._view(self.info.ids, self.info.rows, torch.int32).clone()
+
+    def vectors(self) -> torch.Tensor:
+        i = self.info
+        if i.mode == SOAR_SCORE_FP8:
+            return self._view(i.vectors, i.rows * i.row_stride, torch.uint8).clone().view(i.rows, i.row_stride)
+        dt = torch.float32 if i.dtype == SOAR_F32 else torch.bfloat16
+        return self._view(i.vectors, i.rows * i.row_stride, dt).clone().view(i.rows, i.row_stride)
+
+    def row_scales(self) -> torch.Tensor:
+        return self._view(self.info.row_scales, self.info.rows, torch.float32).clone()
+
+
+class _DeviceArray:
+    """Minimal __cuda_array_interface__ provider for memory the library owns."""
+
+    def __init__(self, ptr: int, count: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (count,), "typestr": typestr, "data": (int(ptr), True),
+                                         "version": 3, "strides": None}
+
+
+_TYPESTR = {torch.float32: "<f4", torch.int32: "<i4", torch.int64: "<i8", torch.uint8: "|u1",
+            torch.bfloat16: "<i2"}
+
+
+def _wrap_device(ptr: int, count: int, dtype: torch.dtype) -> torch.Tensor:
+    """A torch tensor aliasing `count` elements of device memory at `ptr`."""
+    t = torch.as_tensor(_DeviceArray(ptr, count, _TYPESTR[dtype]), device="cuda")
+    return t.view(torch.bfloat16) if dtype == torch.bfloat16 else t
+
+
+def soar_index_build(X: torch.Tensor, C: torch.Tensor, assign: torch.Tensor, mode: int = SOAR_SCORE_F32,
+                     stream=None) -> Index:
+    n, d = X.shape
+    c = C.shape[0]
+    spills = assign.shape[1] - 1
+    if assign.shape[0] != n:
+        raise ValueError("assign must have one row per datapoint")
+    h = ct.c_void_p()
+    _check(load().soar_index_build(_dev(X, "X", ndim=2), _dtype(X), n, d, _dev(C, "C", torch.float32, 2), c,
+                                   _dev(assign, "assign", torch.int32, 2), spills, mode, ct.byref(h),
+                                   _stream(stream)))
+    return Index(h)
+
+
+def soar_select_partitions(index: Index, Q: torch.Tensor, t: int, with_scores: bool = False, stream=None):
+    nq = Q.shape[0]
+    top = torch.empty((nq, t), dtype=torch.int32, device=Q.device)
+    sc = torch.empty((nq, t), dtype=torch.float32, device=Q.device) if with_scores else None
+    _check(load().soar_select_partitions(index.handle, _dev(Q, "Q", ndim=2), _dtype(Q), nq, t,
+                                         _dev(top, "top"), _dev(sc, "scores") if sc is not None else None,
+                                         _stream(stream)))
+    return (top, sc) if with_scores else top
+
+
+def soar_search(index: Index, Q: torch.Tensor, k: int, t: int, t_per_query=None, rescore: int = 0,
+                ids_out=None, scores_out=None, stream=None):
+    nq = Q.shape[0]
+    if ids_out is None:
+        ids_out = torch.empty((nq, k), dtype=torch.int64, device=Q.device)
+    if scores_out is None:
+        scores_out = torch.empty((nq, k), dtype=torch.float32, device=Q.device)
+    tpq = _dev(t_per_query, "t_per_query", torch.int32, 1) if t_per_query is not None else None
+    _check(load().soar_search(index.handle, _dev(Q, "Q", ndim=2), _dtype(Q), nq, k, t, tpq, rescore,
+                              _dev(ids_out, "ids_out", torch.int64, 2),
+                              _dev(scores_out, "scores_out", torch.float32, 2), _stream(stream)))
+    return ids_out, scores_out
+
+
+def soar_exact_mips(X: torch.Tensor, Q: torch.Tensor, k: int, stream=None):
+    n, d = X.shape
+    nq = Q.shape[0]
+    ids = torch.empty((nq, k), dtype=torch.int64, device=Q.device)
+    sc = torch.empty((nq, k), dtype=torch.float32, device=Q.device)
+    _check(load().soar_exact_mips(_dev(X, "X", ndim=2), _dtype(X), n, d, _dev(Q, "Q", ndim=2), _dtype(Q), nq, k,
+                                  _dev(ids, "ids"), _dev(sc, "scores"), _stream(stream)))
+    return ids, sc
+
+
+def soar_quantize_fp8(V: torch.Tensor, code_stride: int | None = None, stream=None):
+    m, d = V.shape
+    cs = d if code_stride is None else code_stride
+    codes = torch.empty((m, cs), dtype=torch.uint8, device=V.device)
+    scales = torch.empty((m,), dtype=torch.float32, device=V.device)
+    _check(load().soar_quantize_fp8(_dev(V, "V", ndim=2), _dtype(V), m, d, _dev(codes, "codes"), cs,
+                                    _dev(scales, "scales"), _stream(stream)))
+    return codes, scales
+
+
+def soar_kernel_launches() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(load().soar_kernel_launches())
+
+
+def soar_stage_timing(enable: bool) -> None:
+    _check(load().soar_stage_timing(1 if enable else 0))
+
+
+def soar_stage_times() -> dict:
+    """{stage: (total_ms, launches)} recorded since the last read (then cleared)."""
+    names = ct.create_string_buffer(1024)
+    ms = (ct.c_float * 32)()
+    cnt = (ct.c_int32 * 32)()
+    m = load().soar_stage_times(names, 1024, ct.cast(ms, ct.c_void_p), ct.cast(cnt, ct.c_void_p), 32)
+    keys = names.value.decode().split(",") if m else []
+    return {keys[i]: (float(ms[i]), int(cnt[i])) for i in range(m)}

@@ -1,0 +1,287 @@
+// C ABI of the library (declared in include/soar.h): argument checks,
+// error translation and the index handle.  All compute lives in the other
+// translation units; nothing here touches vector data on the host.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "internal.cuh"
+
+struct soar_index {
+  soar::IndexData data;
+};
+
+namespace soar {
+
+std::atomic<uint64_t> g_launches{0};
+
+namespace {
+struct StageEvent {
+  std::string stage;
+  cudaEvent_t begin, end;
+};
+std::mutex g_stage_mu;
+bool g_stage_on = false;
+std::vector<StageEvent> g_stage_events;
+std::vector<std::pair<std::string, cudaEvent_t>> g_open;
+}  // namespace
+
+void stage_mark(cudaStream_t s, const char* stage, bool begin) {
+  std::lock_guard<std::mutex> lock(g_stage_mu);
+  if (!g_stage_on) return;
+  cudaEvent_t e;
+  SOAR_CUDA(cudaEventCreate(&e));
+  SOAR_CUDA(cudaEventRecord(e, s));
+  if (begin) {
+    g_open.emplace_back(stage, e);
+    return;
+  }
+  for (size_t i = g_open.size(); i-- > 0;) {
+    if (g_open[i].first == stage) {
+      g_stage_events.push_back(StageEvent{stage, g_open[i].second, e});
+      g_open.erase(g_open.begin() + (long)i);
+      return;
+    }
+  }
+  cudaEventDestroy(e);
+}
+
+}  // namespace soar
+
+namespace {
+
+thread_local std::string g_last_error;
+
+// Keep freed pool memory cached so per-call scratch costs no driver calls.
+void configure_pool() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) return;
+    uint64_t threshold = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &threshold);
+  });
+}
+
+template <typename F>
+soar_status guarded(F&& f) {
+  try {
+    configure_pool();
+    f();
+    g_last_error.clear();
+    return SOAR_OK;
+  } catch (const soar::Error& e) {
+    g_last_error = e.what();
+    return e.status;
+  } catch (const std::bad_alloc&) {
+    g_last_error = "host allocation failed";
+    return SOAR_ENOMEM;
+  } catch (const std::exception& e) {
+    g_last_error = e.what();
+    return SOAR_ECUDA;
+  } catch (...) {
+    g_last_error = "unknown error";
+    return SOAR_ECUDA;
+  }
+}
+
+bool valid_dtype(soar_dtype dt) { return dt == SOAR_F32 || dt == SOAR_BF16; }
+
+}  // namespace
+
+extern "C" {
+
+const char* soar_last_error(void) { return g_last_error.c_str(); }
+
+const char* soar_version(void) { return "soar-gb300 0.1 sm_103a"; }
+
+soar_status soar_train_centroids(const void* X, soar_dtype dtype, int64_t n, int32_t d, int32_t c, int32_t iters,
+                                 const int32_t* init_idx, float* C_out, cudaStream_t stream) {
+  return guarded([&] {
+    SOAR_REQUIRE(X && init_idx && C_out, "null pointer");
+    SOAR_REQUIRE(valid_dtype(dtype), "unknown dtype");
+    SOAR_REQUIRE(n >= 1 && n < (int64_t(1) << 31), "n must be in [1, 2^31)");
+    SOAR_REQUIRE(d >= 1 && d <= 4096, "d must be in [1, 4096]");
+    SOAR_REQUIRE(c >= 1 && c <= n, "c must be in [1, n]");
+    SOAR_REQUIRE(iters >= 0, "iters must be >= 0");
+    soar::Scratch scr(stream);
+    soar::kmeans_train(X, dtype, n, d, c, iters, init_idx, C_out, stream, scr);
+  });
+}
+
+soar_status soar_assign(const void* X, soar_dtype dtype, int64_t n, int32_t d, const float* C, int32_t c,
+                        float lambda, int32_t spills, int32_t* assign_out, cudaStream_t stream) {
+  return guarded([&] {
+    SOAR_REQUIRE(X && C && assign_out, "null pointer");
+    SOAR_REQUIRE(valid_dtype(dtype), "unknown dtype");
+    SOAR_REQUIRE(n >= 1 && n < (int64_t(1) << 31), "n must be in [1, 2^31)");
+    SOAR_REQUIRE(d >= 1 && d <= 4096, "d must be in [1, 4096]");
+    SOAR_REQUIRE(std::isfinite(lambda) && lambda >= 0.f, "lambda must be finite and >= 0");
+    SOAR_REQUIRE(spills >= 0 && spills <= 4, "spills must be in [0, 4]");
+    SOAR_REQUIRE(c >= 1 + spills, "c must be >= 1 + spills");
+    soar::Scratch scr(stream);
+    soar::assign_points(X, dtype, n, d, C, c, lambda, spills, assign_out, stream, scr);
+  });
+}
+
+soar_status soar_index_build(const void* X, soar_dtype dtype, int64_t n, int32_t d, const float* C, int32_t c,
+                             const int32_t* assign, int32_t spills, soar_score_mode mode, soar_index** out,
+                             cudaStream_t stream) {
+  return guarded([&] {
+    SOAR_REQUIRE(X && C && assign && out, "null pointer");
+    SOAR_REQUIRE(valid_dtype(dtype), "unknown dtype");
+    SOAR_REQUIRE(n >= 1 && d >= 1 && d <= 4096 && c >= 1, "bad sizes");
+    SOAR_REQUIRE(spills >= 0 && spills <= 4 && c >= 1 + spills, "spills must be in [0, 4] and <= c - 1");
+    SOAR_REQUIRE(n * (1 + spills) < (int64_t(1) << 31), "n * (1 + spills) must be < 2^31");
+    SOAR_REQUIRE(mode == SOAR_SCORE_F32 || mode == SOAR_SCORE_FP8 || mode == SOAR_SCORE_BF16, "unknown mode");
+    if (mode == SOAR_SCORE_BF16) soar::fail(SOAR_EUNSUPPORTED, "soar_index_build: SOAR_SCORE_BF16 not implemented");
+    soar_index* ix = new soar_index;
+    ix->data.n = n;
+    ix->data.d = d;
+    ix->data.c = c;
+    ix->data.spills = spills;
+    ix->data.mode = mode;
+    ix->data.dtype = dtype;
+    ix->data.rows = n * (1 + spills);
+    try {
+      soar::build_index(ix->data, X, dtype, C, assign, stream);
+    } catch (...) {
+      cudaStreamSynchronize(stream);
+      soar::free_index(ix->data);
+      delete ix;
+      throw;
+    }
+    *out = ix;
+  });
+}
+
+soar_status soar_index_get_info(const soar_index* index, soar_index_info* info) {
+  return guarded([&] {
+    SOAR_REQUIRE(index && info, "null pointer");
+    const soar::IndexData& x = index->data;
+    info->n = x.n;
+    info->d = x.d;
+    info->c = x.c;
+    info->spills = x.spills;
+    info->mode = x.mode;
+    info->dtype = x.dtype;
+    info->row_stride = x.row_stride;
+    info->rows = x.rows;
+    info->max_partition = x.max_partition;
+    info->offsets = x.offsets;
+    info->ids = x.ids;
+    info->vectors = x.vectors;
+    info->row_scales = x.row_scales;
+    info->originals = x.originals;
+    info->centroids = x.centroids;
+    info->device_bytes = x.bytes;
+  });
+}
+
+soar_status soar_index_free(soar_index* index) {
+  return guarded([&] {
+    if (!index) return;
+    SOAR_CUDA(cudaDeviceSynchronize());
+    soar::free_index(index->data);
+    delete index;
+  });
+}
+
+soar_status soar_select_partitions(const soar_index* index, const void* Q, soar_dtype dtype, int64_t nq, int32_t t,
+                                   int32_t* top_out, float* score_out, cudaStream_t stream) {
+  return guarded([&] {
+    SOAR_REQUIRE(index && Q && top_out, "null pointer");
+    SOAR_REQUIRE(valid_dtype(dtype), "unknown dtype");
+    SOAR_REQUIRE(nq >= 1 && nq < (int64_t(1) << 31), "nq must be in [1, 2^31)");
+    SOAR_REQUIRE(t >= 1 && t <= index->data.c && t <= 8192, "t must be in [1, min(c, 8192)]");
+    soar::Scratch scr(stream);
+    soar::select_partitions(index->data, Q, dtype, nq, t, top_out, score_out, stream, scr);
+  });
+}
+
+soar_status soar_search(const soar_index* index, const void* Q, soar_dtype dtype, int64_t nq, int32_t k, int32_t t,
+                        const int32_t* t_per_query, int32_t rescore, int64_t* ids_out, float* scores_out,
+                        cudaStream_t stream) {
+  return guarded([&] {
+    SOAR_REQUIRE(index && Q && ids_out && scores_out, "null pointer");
+    SOAR_REQUIRE(valid_dtype(dtype), "unknown dtype");
+    SOAR_REQUIRE(nq >= 1 && nq * (int64_t)t < (int64_t(1) << 31), "nq * t must be in [1, 2^31)");
+    SOAR_REQUIRE(k >= 1 && k <= 1024, "k must be in [1, 1024]");
+    SOAR_REQUIRE(t >= 1 && t <= index->data.c && t <= 8192, "t must be in [1, min(c, 8192)]");
+    if (index->data.mode == SOAR_SCORE_FP8)
+      SOAR_REQUIRE(rescore >= k && rescore <= 4096, "rescore must be in [k, 4096] for an FP8 index");
+    soar::Scratch scr(stream);
+    soar::search(index->data, Q, dtype, nq, k, t, t_per_query, rescore, ids_out, scores_out, stream, scr);
+  });
+}
+
+soar_status soar_exact_mips(const void* X, soar_dtype xdtype, int64_t n, int32_t d, const void* Q, soar_dtype qdtype,
+                            int64_t nq, int32_t k, int64_t* ids_out, float* scores_out, cudaStream_t stream) {
+  return guarded([&] {
+    SOAR_REQUIRE(X && Q && ids_out && scores_out, "null pointer");
+    SOAR_REQUIRE(valid_dtype(xdtype) && valid_dtype(qdtype), "unknown dtype");
+    SOAR_REQUIRE(n >= 1 && n < (int64_t(1) << 31) && nq >= 1 && d >= 1 && d <= 4096, "bad sizes");
+    SOAR_REQUIRE(k >= 1 && k <= 1024, "k must be in [1, 1024]");
+    soar::Scratch scr(stream);
+    soar::exact_mips(X, xdtype, n, d, Q, qdtype, nq, k, ids_out, scores_out, stream, scr);
+  });
+}
+
+uint64_t soar_kernel_launches(void) { return soar::g_launches.load(); }
+
+soar_status soar_stage_timing(int enable) {
+  return guarded([&] {
+    std::lock_guard<std::mutex> lock(soar::g_stage_mu);
+    soar::g_stage_on = enable != 0;
+  });
+}
+
+int soar_stage_times(char* names, int names_len, float* ms, int* launches, int max_stages) {
+  std::lock_guard<std::mutex> lock(soar::g_stage_mu);
+  std::vector<std::string> order;
+  std::vector<float> tot;
+  std::vector<int> cnt;
+  for (auto& ev : soar::g_stage_events) {
+    float t = 0.f;
+    if (cudaEventSynchronize(ev.end) == cudaSuccess) cudaEventElapsedTime(&t, ev.begin, ev.end);
+    cudaEventDestroy(ev.begin);
+    cudaEventDestroy(ev.end);
+    size_t i = 0;
+    while (i < order.size() && order[i] != ev.stage) ++i;
+    if (i == order.size()) {
+      order.push_back(ev.stage);
+      tot.push_back(0.f);
+      cnt.push_back(0);
+    }
+    tot[i] += t;
+    cnt[i] += 1;
+  }
+  soar::g_stage_events.clear();
+  std::string joined;
+  int m = 0;
+  for (size_t i = 0; i < order.size() && m < max_stages; ++i, ++m) {
+    if (ms) ms[m] = tot[i];
+    if (launches) launches[m] = cnt[i];
+    joined += (i ? "," : "") + order[i];
+  }
+  if (names && names_len > 0) {
+    size_t n = std::min((size_t)names_len - 1, joined.size());
+    memcpy(names, joined.data(), n);
+    names[n] = 0;
+  }
+  return m;
+}
+
+soar_status soar_quantize_fp8(const void* V, soar_dtype dtype, int64_t m, int32_t d, uint8_t* codes,
+                              int32_t code_stride, float* scales, cudaStream_t stream) {
+  return guarded([&] {
+    SOAR_REQUIRE(V && codes && scales, "null pointer");
+    SOAR_REQUIRE(valid_dtype(dtype), "unknown dtype");
+    SOAR_REQUIRE(m >= 0 && d >= 1 && code_stride >= d, "bad sizes");
+    soar::quantize_fp8(V, dtype, m, d, codes, code_stride, scales, stream);
+  });
+}
+
+}  // extern "C"

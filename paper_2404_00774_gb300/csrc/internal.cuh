@@ -1,0 +1,75 @@
+// Internal launchers shared between the translation units of the library.
+#pragma once
+
+#include "common.cuh"
+
+namespace soar {
+
+// ----------------------------------------------------------- sort.cu
+
+// Exclusive prefix sum of `count` values; out may alias in.  Returns nothing;
+// the total is out[count-1] + in[count-1] (callers that need it keep a copy).
+void exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t count, cudaStream_t s, Scratch& scr);
+void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t count, cudaStream_t s, Scratch& scr);
+
+// Stable sort of (key, value) pairs by key, keys in [0, 2^key_bits).
+// Ping-pongs between (keys, vals) and (keys_tmp, vals_tmp); returns true when
+// the sorted result ended in the *_tmp buffers.
+bool radix_sort_pairs(uint32_t* keys, int32_t* vals, uint32_t* keys_tmp, int32_t* vals_tmp,
+                      int64_t count, int key_bits, cudaStream_t s, Scratch& scr);
+
+// offsets[p] = first position whose key >= p, for p in [0, num_keys]; keys sorted.
+void segment_offsets(const uint32_t* keys_sorted, int64_t count, int32_t num_keys,
+                     int64_t* offsets, cudaStream_t s);
+
+int bits_for(int64_t num_keys);
+
+// ----------------------------------------------------------- assign.cu
+
+// pi(x) for every row (nearest centroid, lower index on ties), optionally the
+// SOAR spills, written to assign[n][1+spills].
+void assign_points(const void* X, soar_dtype dt, int64_t n, int32_t d, const float* C, int32_t c,
+                   float lambda, int32_t spills, int32_t* assign, cudaStream_t s, Scratch& scr);
+
+void kmeans_train(const void* X, soar_dtype dt, int64_t n, int32_t d, int32_t c, int32_t iters,
+                  const int32_t* init_idx, float* C, cudaStream_t s, Scratch& scr);
+
+// ----------------------------------------------------------- ivf.cu
+
+struct IndexData {
+  int64_t n = 0;
+  int32_t d = 0, c = 0, spills = 0, mode = 0, dtype = 0, row_stride = 0;
+  int64_t rows = 0, max_partition = 0, bytes = 0;
+  int64_t* offsets = nullptr;   // [c+1]
+  int32_t* ids = nullptr;       // [rows]
+  void* vectors = nullptr;      // [rows][row_stride]
+  float* row_scales = nullptr;  // [rows] (FP8)
+  void* originals = nullptr;    // [n][row_stride] (FP8)
+  float* centroids = nullptr;   // [c][d]
+  int32_t* part_order = nullptr;  // [c] partitions by size, largest first
+  float* cent_code_vals = nullptr;  // [c][code_stride] decoded E4M3 code values (FP8)
+  float* cent_scales = nullptr;     // [c] (FP8)
+  int32_t code_stride = 0;
+};
+
+void build_index(IndexData& ix, const void* X, soar_dtype dt, const float* C, const int32_t* assign,
+                 cudaStream_t s);
+void free_index(IndexData& ix);
+
+void quantize_fp8(const void* V, soar_dtype dt, int64_t m, int32_t d, uint8_t* codes,
+                  int32_t code_stride, float* scales, cudaStream_t s);
+
+// ----------------------------------------------------------- search.cu
+
+void select_partitions(const IndexData& ix, const void* Q, soar_dtype dt, int64_t nq, int32_t t,
+                       int32_t* top, float* top_scores, cudaStream_t s, Scratch& scr);
+
+void search(const IndexData& ix, const void* Q, soar_dtype dt, int64_t nq, int32_t k, int32_t t,
+            const int32_t* t_per_query, int32_t rescore, int64_t* ids_out, float* scores_out,
+            cudaStream_t s, Scratch& scr);
+
+void exact_mips(const void* X, soar_dtype xdt, int64_t n, int32_t d, const void* Q, soar_dtype qdt,
+                int64_t nq, int32_t k, int64_t* ids_out, float* scores_out, cudaStream_t s,
+                Scratch& scr);
+
+}  // namespace soar

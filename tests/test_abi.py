@@ -1,0 +1,76 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry point
+that include/soar.h declares; host-side argument checks reject bad input
+before any device work (no compute calls here)."""
+import ctypes as ct
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h")]
+
+
+def _declared():
+    names = []
+    for h in HEADERS:
+        src = open(h).read()
+        names += re.findall(r"^SOAR_API\s+[\w\s\*]+?\b(soar_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2404_00774_gb300 import build
+    path = build.build()
+    return ct.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("soar_train_centroids", "soar_assign", "soar_index_build", "soar_search",
+                     "soar_index_free", "soar_last_error", "soar_exact_mips", "soar_select_partitions"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, f"declared but not exported: {missing}"
+
+
+def test_binding_names_match_the_abi():
+    from paper_2404_00774_gb300 import binding
+    for name in binding._SIGS:
+        assert name in _declared()
+    for name in _declared():
+        if name not in ("soar_last_error", "soar_version", "soar_index_get_info", "soar_index_free"):
+            assert hasattr(binding, name), f"binding lacks {name}"
+
+
+def test_version_and_error_string_without_gpu(lib):
+    lib.soar_version.restype = ct.c_char_p
+    assert b"sm_103a" in lib.soar_version()
+    lib.soar_last_error.restype = ct.c_char_p
+    assert lib.soar_last_error() == b""
+
+
+def test_invalid_arguments_rejected_on_host(lib):
+    # null pointers and bad sizes fail with SOAR_EINVAL before touching a device
+    lib.soar_last_error.restype = ct.c_char_p
+    f = lib.soar_assign
+    f.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int64, ct.c_int32, ct.c_void_p, ct.c_int32, ct.c_float,
+                  ct.c_int32, ct.c_void_p, ct.c_void_p]
+    f.restype = ct.c_int32
+    assert f(None, 0, 10, 4, None, 4, 1.0, 1, None, None) == 1
+    assert b"null pointer" in lib.soar_last_error()
+    dummy = ct.c_void_p(16)
+    assert f(dummy, 0, 10, 4, dummy, 4, float("nan"), 1, dummy, None) == 1
+    assert b"lambda" in lib.soar_last_error()
+    assert f(dummy, 0, 10, 4, dummy, 1, 1.0, 1, dummy, None) == 1        # c < 1 + spills
+    assert f(dummy, 0, 10, 4, dummy, 8, 1.0, 5, dummy, None) == 1        # spills > 4
+    assert f(dummy, 7, 10, 4, dummy, 8, 1.0, 1, dummy, None) == 1        # unknown dtype
+    s = lib.soar_search
+    s.argtypes = [ct.c_void_p, ct.c_void_p, ct.c_int32, ct.c_int64, ct.c_int32, ct.c_int32, ct.c_void_p,
+                  ct.c_int32, ct.c_void_p, ct.c_void_p, ct.c_void_p]
+    s.restype = ct.c_int32
+    assert s(None, dummy, 0, 1, 10, 4, None, 0, dummy, dummy, None) == 1

@@ -1,0 +1,274 @@
+"""GPU path vs CPU oracle, element by element, through the C ABI.
+
+Sizes span several tiles with ragged tails (n, nq not multiples of 64; d not
+a multiple of 4) and the degenerate cases of the method (lambda = 0, a zero
+residual, more neighbours requested than candidates, t = c).  Each stage is
+tested in isolation: the GPU stage receives the oracle's inputs.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from parity_util import assign_mismatches, score_errors, topk_mismatches
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+def _t(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+    return t.to(dtype) if dtype is not None else t
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    X, Q, init = synth.workload_arrays("tiny")
+    C = oracle.kmeans(X, init, 10)
+    return X, Q, init, C
+
+
+def _exact(X, Q):
+    Xd, Qd = X.astype(np.float64), Q.astype(np.float64)
+    return lambda q, ids: Xd[np.asarray(ids, dtype=np.int64)] @ Qd[q]
+
+
+# ------------------------------------------------------------------ k-means
+
+def test_kmeans_one_step_matches(soar, tiny):
+    X, Q, init, _ = tiny
+    C_gpu = soar.soar_train_centroids(_t(X), 64, 1, _t(init)).cpu().numpy()
+    C_ref = oracle.kmeans(X, init, 1)
+    # same assignment from the seed rows (no near-ties on this data), so each
+    # centroid is the same fp64 mean rounded to fp32: at most 1 ulp apart
+    pi0, best, gap = oracle.primary_assign(X, X[init])
+    assert np.all(gap > 1e-5 * best)
+    np.testing.assert_array_max_ulp(C_gpu, C_ref, maxulp=1)
+
+
+def test_kmeans_ten_iterations_objective(soar, tiny):
+    X, Q, init, C_ref = tiny
+    C_gpu = soar.soar_train_centroids(_t(X), 64, 10, _t(init)).cpu().numpy()
+    obj_gpu = oracle.kmeans_objective(X, C_gpu)
+    obj_ref = oracle.kmeans_objective(X, C_ref)
+    assert obj_gpu == pytest.approx(obj_ref, rel=1e-4)
+    assert np.abs(C_gpu - C_ref).max() < 1e-3
+
+
+def test_kmeans_zero_iterations_returns_seed_rows(soar, tiny):
+    X, Q, init, _ = tiny
+    C_gpu = soar.soar_train_centroids(_t(X), 64, 0, _t(init)).cpu().numpy()
+    np.testing.assert_array_equal(C_gpu, X[init])
+
+
+# --------------------------------------------------------------- assignment
+
+@pytest.mark.parametrize("lam", [0.0, 0.5, 1.0, 2.0])
+@pytest.mark.parametrize("spills", [0, 1, 2])
+def test_soar_assign_matches_oracle(soar, tiny, lam, spills):
+    X, Q, init, C = tiny
+    got = soar.soar_assign(_t(X), _t(C), lam, spills).cpu().numpy()
+    want, gaps, best = oracle.soar_assign(X, C, lam, spills, return_gaps=True)
+    bad, exempt = assign_mismatches(got, want, gaps, best)
+    assert len(bad) == 0, f"{len(bad)} rows differ beyond near-ties (e.g. {bad[:5]}), {exempt} exempt"
+
+
+def test_soar_assign_bf16_inputs(soar, tiny):
+    X, Q, init, C = tiny
+    Xb = oracle.bf16_round(X)
+    got = soar.soar_assign(_t(X, torch.bfloat16), _t(C), 1.0, 1).cpu().numpy()
+    want, gaps, best = oracle.soar_assign(Xb, C, 1.0, 1, return_gaps=True)
+    bad, _ = assign_mismatches(got, want, gaps, best)
+    assert len(bad) == 0
+
+
+def test_soar_assign_ragged_and_degenerate(soar):
+    rng = np.random.default_rng(21)
+    n, d, c = 1037, 37, 70          # ragged n and d, c not a tile multiple
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    C = rng.standard_normal((c, d)).astype(np.float32)
+    X[:5] = C[3]                    # zero residual: the penalty vanishes
+    C[50] = C[10]                   # duplicate centroid: lower index wins
+    for lam, s in [(0.0, 1), (1.0, 1), (3.0, 4)]:
+        got = soar.soar_assign(_t(X), _t(C), lam, s).cpu().numpy()
+        want, gaps, best = oracle.soar_assign(X, C, lam, s, return_gaps=True)
+        bad, _ = assign_mismatches(got, want, gaps, best)
+        assert len(bad) == 0, (lam, s, bad[:5])
+    # c == 1 + spills: the spill takes the only centroid left
+    got = soar.soar_assign(_t(X[:100]), _t(C[:2]), 1.0, 1).cpu().numpy()
+    assert np.all(np.sort(got, axis=1) == [0, 1])
+
+
+def test_fig3_worked_example_on_gpu(soar):
+    x = np.array([[2.8, 1.9]], dtype=np.float32)
+    C = np.array([[2.0, 2.5], [1.68, 2.74], [3.01, 0.24]], dtype=np.float32)
+    for lam, want in [(0.0, 1), (1.0, 1), (1.3, 1), (1.5, 2), (2.0, 2)]:
+        a = soar.soar_assign(_t(x), _t(C), lam, 1).cpu().numpy()
+        assert a[0, 0] == 0 and a[0, 1] == want
+
+
+# --------------------------------------------------------------- index build
+
+@pytest.mark.parametrize("spills", [0, 1, 2])
+def test_index_build_is_bit_exact(soar, tiny, spills):
+    X, Q, init, C = tiny
+    A = oracle.soar_assign(X, C, 1.0, spills)
+    ix = soar.soar_index_build(_t(X), _t(C), _t(A))
+    off, ids = oracle.build_ivf(A, C.shape[0])
+    np.testing.assert_array_equal(ix.offsets().cpu().numpy(), off)
+    np.testing.assert_array_equal(ix.ids().cpu().numpy(), ids)
+    np.testing.assert_array_equal(ix.vectors().cpu().numpy()[:, :X.shape[1]], X[ids])
+    assert ix.info.max_partition == np.diff(off).max()
+    ix.close()
+
+
+def test_index_build_rejects_bad_assignments(soar, tiny):
+    X, Q, init, C = tiny
+    A = oracle.soar_assign(X, C, 1.0, 1)
+    bad = A.copy()
+    bad[7, 1] = 64                  # outside [0, c)
+    with pytest.raises(soar.SoarError) as e:
+        soar.soar_index_build(_t(X), _t(C), _t(bad))
+    assert e.value.status == soar.SOAR_EINVAL
+    bad = A.copy()
+    bad[9, 1] = bad[9, 0]           # same partition twice
+    with pytest.raises(soar.SoarError):
+        soar.soar_index_build(_t(X), _t(C), _t(bad))
+
+
+# --------------------------------------------------------------- search
+
+@pytest.fixture(scope="module")
+def tiny_index(soar, tiny):
+    X, Q, init, C = tiny
+    A = oracle.soar_assign(X, C, 1.0, 1)
+    off, ids = oracle.build_ivf(A, C.shape[0])
+    ix = soar.soar_index_build(_t(X), _t(C), _t(A))
+    yield X, Q, C, A, off, ids, ix
+    ix.close()
+
+
+@pytest.mark.parametrize("t", [1, 4, 17, 64])
+def test_select_partitions_matches(soar, tiny_index, t):
+    X, Q, C, A, off, ids, ix = tiny_index
+    top, sc = soar.soar_select_partitions(ix, _t(Q), t, with_scores=True)
+    want, wsc = oracle.select_partitions(Q, C, t)
+    exact = lambda q, p: np.asarray(C, np.float64)[np.asarray(p, np.int64)] @ Q[q].astype(np.float64)
+    assert topk_mismatches(top.cpu().numpy(), want, wsc, exact) == []
+    np.testing.assert_allclose(sc.cpu().numpy(), wsc, rtol=1e-5, atol=1e-6)
+
+
+@pytest.mark.parametrize("k,t", [(10, 4), (1, 1), (100, 8), (10, 64)])
+def test_search_matches_oracle(soar, tiny_index, k, t):
+    X, Q, C, A, off, ids, ix = tiny_index
+    gi, gs = soar.soar_search(ix, _t(Q), k, t)
+    wi, ws = oracle.ivf_search(Q, X, C, off, ids, k, t)
+    gi, gs = gi.cpu().numpy(), gs.cpu().numpy()
+    ex = _exact(X, Q)
+    assert topk_mismatches(gi, wi, ws, ex) == []
+    mx, mean = score_errors(gi, gs, ex)
+    assert mx < 1e-5, (mx, mean)
+
+
+def test_search_all_partitions_is_brute_force(soar, tiny_index):
+    X, Q, C, A, off, ids, ix = tiny_index
+    gi, gs = soar.soar_search(ix, _t(Q), 10, C.shape[0])
+    wi, ws = oracle.mips_topk(Q, X, 10)
+    assert topk_mismatches(gi.cpu().numpy(), wi, ws, _exact(X, Q)) == []
+
+
+def test_search_per_query_probe_counts(soar, tiny_index):
+    X, Q, C, A, off, ids, ix = tiny_index
+    tpq = np.random.default_rng(3).integers(1, 9, size=Q.shape[0]).astype(np.int32)
+    gi, gs = soar.soar_search(ix, _t(Q), 10, 8, t_per_query=_t(tpq))
+    wi, ws = oracle.ivf_search(Q, X, C, off, ids, 10, 8, t_per_query=tpq)
+    assert topk_mismatches(gi.cpu().numpy(), wi, ws, _exact(X, Q)) == []
+
+
+def test_search_pads_when_candidates_run_out(soar):
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((90, 37)).astype(np.float32)
+    Q = rng.standard_normal((3, 37)).astype(np.float32)
+    C = oracle.kmeans(X, np.arange(5), 3)
+    A = oracle.soar_assign(X, C, 1.0, 1)
+    off, ids = oracle.build_ivf(A, 5)
+    ix = soar.soar_index_build(_t(X), _t(C), _t(A))
+    gi, gs = soar.soar_search(ix, _t(Q), 100, 1)
+    wi, ws = oracle.ivf_search(Q, X, C, off, ids, 100, 1)
+    gi, gs = gi.cpu().numpy(), gs.cpu().numpy()
+    np.testing.assert_array_equal(gi < 0, wi < 0)
+    assert np.all(np.isneginf(gs[gi < 0]))
+    assert topk_mismatches(gi, wi, ws, _exact(X, Q)) == []
+    ix.close()
+
+
+def test_search_bf16_index(soar, tiny):
+    X, Q, init, C = tiny
+    Xb = oracle.bf16_round(X)
+    A = oracle.soar_assign(Xb, C, 1.0, 1)
+    off, ids = oracle.build_ivf(A, C.shape[0])
+    ix = soar.soar_index_build(_t(X, torch.bfloat16), _t(C), _t(A))
+    gi, gs = soar.soar_search(ix, _t(Q), 10, 4)
+    wi, ws = oracle.ivf_search(Q, Xb, C, off, ids, 10, 4)
+    assert topk_mismatches(gi.cpu().numpy(), wi, ws, _exact(Xb, Q)) == []
+    ix.close()
+
+
+# --------------------------------------------------------------- brute force
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_exact_mips_matches(soar, tiny, dtype):
+    X, Q, init, C = tiny
+    Xr = X if dtype == torch.float32 else oracle.bf16_round(X)
+    gi, gs = soar.soar_exact_mips(_t(X, dtype), _t(Q), 10)
+    wi, ws = oracle.mips_topk(Q, Xr, 10)
+    gi = gi.cpu().numpy()
+    assert topk_mismatches(gi, wi, ws, _exact(Xr, Q)) == []
+    mx, _ = score_errors(gi, gs.cpu().numpy(), _exact(Xr, Q))
+    assert mx < 1e-5
+
+
+def test_exact_mips_ragged(soar):
+    rng = np.random.default_rng(8)
+    X = rng.standard_normal((5003, 37)).astype(np.float32)
+    Q = rng.standard_normal((65, 37)).astype(np.float32)
+    gi, gs = soar.soar_exact_mips(_t(X), _t(Q), 7)
+    wi, ws = oracle.mips_topk(Q, X, 7)
+    assert topk_mismatches(gi.cpu().numpy(), wi, ws, _exact(X, Q)) == []
+
+
+# --------------------------------------------------------------- FP8 path
+
+def test_fp8_codes_bit_exact(soar, tiny):
+    X, Q, init, C = tiny
+    codes, scales = soar.soar_quantize_fp8(_t(X))
+    want_codes, want_scales = oracle.quantize_rows_fp8(X)
+    got_vals = codes.cpu().view(torch.float8_e4m3fn).to(torch.float32).numpy()
+    np.testing.assert_array_equal(scales.cpu().numpy(), want_scales)
+    np.testing.assert_array_equal(got_vals, want_codes)
+
+
+def test_fp8_index_search_with_rescoring(soar, tiny):
+    X, Q, init, C = tiny
+    Xb, Qb = oracle.bf16_round(X), oracle.bf16_round(Q)
+    A = oracle.soar_assign(Xb, C, 1.0, 1)
+    off, ids = oracle.build_ivf(A, C.shape[0])
+    ix = soar.soar_index_build(_t(X, torch.bfloat16), _t(C), _t(A), mode=soar.SOAR_SCORE_FP8)
+    gi, gs = soar.soar_search(ix, _t(Q, torch.bfloat16), 10, 4, rescore=200)
+    wi, ws = oracle.precision_search(Qb, Xb, C, off, ids, 10, 4, 200)
+    gi = gi.cpu().numpy()
+    bad = topk_mismatches(gi, wi, ws, _exact(Xb, Qb))
+    # a query may differ only when its FP8 shortlist boundary is a near-tie
+    assert len(bad) <= 2, bad
+    ix.close()
+
+
+# --------------------------------------------------------------- errors
+
+def test_search_rejects_bad_t_and_k(soar, tiny_index):
+    X, Q, C, A, off, ids, ix = tiny_index
+    with pytest.raises(soar.SoarError):
+        soar.soar_search(ix, _t(Q), 10, 65)
+    with pytest.raises(soar.SoarError):
+        soar.soar_search(ix, _t(Q), 0, 4)
