@@ -184,7 +184,7 @@ class _DeviceArray:
     """Minimal __cuda_array_interface__ provider for memory the library owns."""
 
     def __init__(self, ptr: int, count: int, typestr: str):
-        self.__cuda_array_interface__ = {"shape": (count,), "typestr": typestr, "data": (int(ptr), True),
+        self.__cuda_array_interface__ = {"shape": (count,), "typestr": typestr, "data": (int(ptr), False),
                                          "version": 3, "strides": None}
 
 

@@ -40,11 +40,18 @@ def test_kmeans_one_step_matches(soar, tiny):
     X, Q, init, _ = tiny
     C_gpu = soar.soar_train_centroids(_t(X), 64, 1, _t(init)).cpu().numpy()
     C_ref = oracle.kmeans(X, init, 1)
-    # same assignment from the seed rows (no near-ties on this data), so each
-    # centroid is the same fp64 mean rounded to fp32: at most 1 ulp apart
-    pi0, best, gap = oracle.primary_assign(X, X[init])
-    assert np.all(gap > 1e-5 * best)
-    np.testing.assert_array_max_ulp(C_gpu, C_ref, maxulp=1)
+    # A point whose two nearest seed rows are a near-tie may join either
+    # cluster; every other centroid is the same fp64 mean rounded to fp32, so
+    # at most 1 ulp apart.
+    C0 = X[init]
+    a, gaps, best = oracle.soar_assign(X, C0, 0.0, 1, return_gaps=True)
+    near = gaps[:, 0] <= 1e-5 * best[:, 0]
+    touched = np.zeros(64, dtype=bool)
+    touched[a[near, 0]] = True
+    touched[a[near, 1]] = True
+    assert touched.sum() <= 4
+    np.testing.assert_array_max_ulp(C_gpu[~touched], C_ref[~touched], maxulp=1)
+    np.testing.assert_allclose(C_gpu[touched], C_ref[touched], atol=1e-4)
 
 
 def test_kmeans_ten_iterations_objective(soar, tiny):
