@@ -205,6 +205,33 @@ SOAR_API soar_status soar_quantize_fp8(const void* V, soar_dtype dtype, int64_t 
                               uint8_t* codes, int32_t code_stride, float* scales,
                               cudaStream_t stream);
 
+/*
+ * soar_select_partitions_static: soar_select_partitions without any device
+ * allocation.  The paper has no counterpart; this exists for callers that
+ * must not allocate device memory at call time -- for example a host
+ * framework that owns the whole device memory budget and forbids other
+ * allocators, or a latency-critical serving thread that must never enter
+ * the CUDA allocator (cudaMalloc / cudaFree can block on the device and on
+ * the driver's locks).  Same arguments and results as
+ * soar_select_partitions.
+ *
+ * Scratch (the queries' padded rows and the nq x c score matrix, at most
+ * SOAR_STATIC_SCRATCH_BYTES) lives in a fixed device array inside this
+ * library: every GPU that loads the library holds those bytes until the
+ * process exits.  A batch that needs more returns SOAR_EINVAL with the
+ * byte count in soar_last_error(); split it into smaller calls.  The first
+ * call on each device (with that device current) looks the array's device
+ * address up once; make that first call before any stream capture.
+ * All calls on one device share the array and every call overwrites what it
+ * reads, so calls that overlap on the GPU (different streams, or host
+ * threads without ordering between them) race and must be serialised by the
+ * caller, e.g. by issuing them on one stream.
+ */
+#define SOAR_STATIC_SCRATCH_BYTES (32u << 20)
+SOAR_API soar_status soar_select_partitions_static(const soar_index* index, const void* Q, soar_dtype dtype,
+                                                   int64_t nq, int32_t t, int32_t* top_out, float* score_out,
+                                                   cudaStream_t stream);
+
 /* ------------------------------------------------------------------ *
  * Instrumentation (measurement support; not part of the paper's method)
  * ------------------------------------------------------------------ */

@@ -52,6 +52,7 @@ _SIGS = {
     "soar_search": ([_P, _P, _I32, _I64, _I32, _I32, _P, _I32, _P, _P, _P], _I32),
     "soar_exact_mips": ([_P, _I32, _I64, _I32, _P, _I32, _I64, _I32, _P, _P, _P], _I32),
     "soar_quantize_fp8": ([_P, _I32, _I64, _I32, _P, _I32, _P, _P], _I32),
+    "soar_select_partitions_static": ([_P, _P, _I32, _I64, _I32, _P, _P, _P], _I32),
     "soar_kernel_launches": ([], ct.c_uint64),
     "soar_stage_timing": ([_I32], _I32),
     "soar_stage_times": ([ct.c_char_p, _I32, _P, _P, _I32], _I32),
@@ -220,6 +221,22 @@ def soar_select_partitions(index: Index, Q: torch.Tensor, t: int, with_scores: b
                                          _dev(top, "top"), _dev(sc, "scores") if sc is not None else None,
                                          _stream(stream)))
     return (top, sc) if with_scores else top
+
+
+def soar_select_partitions_static(index: Index, Q: torch.Tensor, t: int, top_out: torch.Tensor,
+                                  scores_out: torch.Tensor | None = None, stream=None):
+    """soar_select_partitions into caller-provided outputs, with no device allocation
+    inside the call (scratch is the library's fixed static buffer; see include/soar.h)."""
+    nq = Q.shape[0]
+    if tuple(top_out.shape) != (nq, t):
+        raise ValueError("top_out must be [nq, t]")
+    if scores_out is not None and tuple(scores_out.shape) != (nq, t):
+        raise ValueError("scores_out must be [nq, t]")
+    _check(load().soar_select_partitions_static(index.handle, _dev(Q, "Q", ndim=2), _dtype(Q), nq, t,
+                                                _dev(top_out, "top_out", torch.int32, 2),
+                                                _dev(scores_out, "scores_out", torch.float32, 2)
+                                                if scores_out is not None else None, _stream(stream)))
+    return top_out, scores_out
 
 
 def soar_search(index: Index, Q: torch.Tensor, k: int, t: int, t_per_query=None, rescore: int = 0,

@@ -89,6 +89,30 @@ soar_status guarded(F&& f) {
 
 bool valid_dtype(soar_dtype dt) { return dt == SOAR_F32 || dt == SOAR_BF16; }
 
+// Scratch of soar_select_partitions_static: a fixed device array that every
+// GPU loading this library holds until the process exits.  Host code must not
+// use `g_static_scratch` as an address (on the host it names a stand-in); the
+// device address is looked up once per device with cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_static_scratch[SOAR_STATIC_SCRATCH_BYTES];
+
+std::mutex g_static_mu;
+void* g_static_ptr[256] = {};
+
+// Device address of g_static_scratch on the current device (looked up on the
+// first call made with that device current).
+void* static_scratch() {
+  int dev = 0;
+  SOAR_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) soar::fail(SOAR_EUNSUPPORTED, "device ordinal above 255");
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    SOAR_CUDA(cudaGetSymbolAddress(&p, g_static_scratch));
+    g_static_ptr[dev] = p;
+  }
+  return g_static_ptr[dev];
+}
+
 }  // namespace
 
 extern "C" {
@@ -226,6 +250,23 @@ soar_status soar_exact_mips(const void* X, soar_dtype xdtype, int64_t n, int32_t
     SOAR_REQUIRE(k >= 1 && k <= 1024, "k must be in [1, 1024]");
     soar::Scratch scr(stream);
     soar::exact_mips(X, xdtype, n, d, Q, qdtype, nq, k, ids_out, scores_out, stream, scr);
+  });
+}
+
+soar_status soar_select_partitions_static(const soar_index* index, const void* Q, soar_dtype dtype, int64_t nq,
+                                          int32_t t, int32_t* top_out, float* score_out, cudaStream_t stream) {
+  return guarded([&] {
+    SOAR_REQUIRE(index && Q && top_out, "null pointer");
+    SOAR_REQUIRE(valid_dtype(dtype), "unknown dtype");
+    SOAR_REQUIRE(nq >= 1 && nq < (int64_t(1) << 31), "nq must be in [1, 2^31)");
+    SOAR_REQUIRE(t >= 1 && t <= index->data.c && t <= 8192, "t must be in [1, min(c, 8192)]");
+    const size_t need = soar::select_scratch_bytes(index->data, nq);
+    if (need > (size_t)SOAR_STATIC_SCRATCH_BYTES)
+      soar::fail(SOAR_EINVAL, "soar_select_partitions_static: " + std::to_string(nq) + " queries need " +
+                                  std::to_string(need) + " bytes of scratch, more than the " +
+                                  std::to_string((size_t)SOAR_STATIC_SCRATCH_BYTES) +
+                                  "-byte static buffer; pass fewer queries per call");
+    soar::select_partitions_in(index->data, Q, dtype, nq, t, top_out, score_out, static_scratch(), stream);
   });
 }
 

@@ -64,6 +64,12 @@ void quantize_fp8(const void* V, soar_dtype dt, int64_t m, int32_t d, uint8_t* c
 void select_partitions(const IndexData& ix, const void* Q, soar_dtype dt, int64_t nq, int32_t t,
                        int32_t* top, float* top_scores, cudaStream_t s, Scratch& scr);
 
+// Same computation as select_partitions with all scratch carved from a
+// caller-provided device buffer of select_scratch_bytes(ix, nq) bytes.
+size_t select_scratch_bytes(const IndexData& ix, int64_t nq);
+void select_partitions_in(const IndexData& ix, const void* Q, soar_dtype dt, int64_t nq, int32_t t, int32_t* top,
+                          float* top_scores, void* scratch, cudaStream_t s);
+
 void search(const IndexData& ix, const void* Q, soar_dtype dt, int64_t nq, int32_t k, int32_t t,
             const int32_t* t_per_query, int32_t rescore, int64_t* ids_out, float* scores_out,
             cudaStream_t s, Scratch& scr);

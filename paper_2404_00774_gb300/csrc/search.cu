@@ -713,6 +713,39 @@ void select_partitions(const IndexData& ix, const void* Q, soar_dtype dt, int64_
   select_prepared(ix, Qf, qscale, nq, qstride, t, top, top_scores, s, scr);
 }
 
+size_t select_scratch_bytes(const IndexData& ix, int64_t nq) {
+  const bool fp8 = ix.mode == SOAR_SCORE_FP8;
+  const int qstride = fp8 ? ix.code_stride : (ix.d + 3) / 4 * 4;
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  return up(sizeof(float) * (size_t)nq * qstride) + up(fp8 ? sizeof(float) * (size_t)nq : 0) +
+         up(sizeof(float) * (size_t)nq * ix.c);
+}
+
+void select_partitions_in(const IndexData& ix, const void* Q, soar_dtype dt, int64_t nq, int32_t t, int32_t* top,
+                          float* top_scores, void* scratch, cudaStream_t s) {
+  const bool fp8 = ix.mode == SOAR_SCORE_FP8;
+  const int qstride = fp8 ? ix.code_stride : (ix.d + 3) / 4 * 4;
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  char* base = static_cast<char*>(scratch);
+  float* Qf = reinterpret_cast<float*>(base);
+  base += up(sizeof(float) * (size_t)nq * qstride);
+  float* qscale = fp8 ? reinterpret_cast<float*>(base) : nullptr;
+  base += up(fp8 ? sizeof(float) * (size_t)nq : 0);
+  float* S = reinterpret_cast<float*>(base);
+  // every scratch element read below is first written here: nothing to clear
+  prep_any(Q, dt, nq, ix.d, qstride, fp8, Qf, qscale, s);
+  dim3 grid(ceil_div(ix.c, 64), ceil_div(nq, 64));
+  gemm_nt<<<grid, 256, 0, s>>>(Qf, nq, qstride, fp8 ? ix.cent_code_vals : ix.centroids, ix.c,
+                               fp8 ? ix.code_stride : ix.d, ix.d, fp8 ? qscale : nullptr,
+                               fp8 ? ix.cent_scales : nullptr, S);
+  SOAR_LAUNCHED();
+  const int t2 = pow2_at_least(t);
+  const int smem = t2 * 8;
+  SOAR_CUDA(cudaFuncSetAttribute(topt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  topt_kernel<<<(unsigned)nq, 256, smem, s>>>(S, ix.c, t, t2, top, top_scores);
+  SOAR_LAUNCHED();
+}
+
 void search(const IndexData& ix, const void* Q, soar_dtype dt, int64_t nq, int32_t k, int32_t t,
             const int32_t* tpq, int32_t rescore, int64_t* ids_out, float* scores_out, cudaStream_t s,
             Scratch& scr) {
