@@ -232,6 +232,14 @@ SOAR_API soar_status soar_select_partitions_static(const soar_index* index, cons
                                                    int64_t nq, int32_t t, int32_t* top_out, float* score_out,
                                                    cudaStream_t stream);
 
+/*
+ * Synchronises the current device and reports device-side failures of
+ * earlier calls: SOAR_ETIMEOUT when a kernel gave up one of its bounded
+ * waits (its results are incomplete), SOAR_ECUDA for a CUDA error.  Clears
+ * the recorded failure.
+ */
+SOAR_API soar_status soar_check_device(void);
+
 /* ------------------------------------------------------------------ *
  * Instrumentation (measurement support; not part of the paper's method)
  * ------------------------------------------------------------------ */

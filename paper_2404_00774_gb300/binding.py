@@ -53,6 +53,7 @@ _SIGS = {
     "soar_exact_mips": ([_P, _I32, _I64, _I32, _P, _I32, _I64, _I32, _P, _P, _P], _I32),
     "soar_quantize_fp8": ([_P, _I32, _I64, _I32, _P, _I32, _P, _P], _I32),
     "soar_select_partitions_static": ([_P, _P, _I32, _I64, _I32, _P, _P, _P], _I32),
+    "soar_check_device": ([], _I32),
     "soar_kernel_launches": ([], ct.c_uint64),
     "soar_stage_timing": ([_I32], _I32),
     "soar_stage_times": ([ct.c_char_p, _I32, _P, _P, _I32], _I32),
@@ -271,6 +272,11 @@ def soar_quantize_fp8(V: torch.Tensor, code_stride: int | None = None, stream=No
     _check(load().soar_quantize_fp8(_dev(V, "V", ndim=2), _dtype(V), m, d, _dev(codes, "codes"), cs,
                                     _dev(scales, "scales"), _stream(stream)))
     return codes, scales
+
+
+def soar_check_device() -> None:
+    """Synchronises and raises SoarError if a kernel gave up a bounded wait."""
+    _check(load().soar_check_device())
 
 
 def soar_kernel_launches() -> int:

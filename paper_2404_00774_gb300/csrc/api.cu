@@ -46,6 +46,25 @@ void stage_mark(cudaStream_t s, const char* stage, bool begin) {
   cudaEventDestroy(e);
 }
 
+namespace {
+std::mutex g_err_mu;
+int* g_err_word[256] = {};
+}  // namespace
+
+int* device_error_word() {
+  int dev = 0;
+  SOAR_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) fail(SOAR_EUNSUPPORTED, "device ordinal above 255");
+  std::lock_guard<std::mutex> lock(g_err_mu);
+  if (!g_err_word[dev]) {
+    int* p = nullptr;
+    SOAR_CUDA(cudaMalloc(&p, sizeof(int)));
+    SOAR_CUDA(cudaMemset(p, 0, sizeof(int)));
+    g_err_word[dev] = p;
+  }
+  return g_err_word[dev];
+}
+
 }  // namespace soar
 
 namespace {
@@ -267,6 +286,19 @@ soar_status soar_select_partitions_static(const soar_index* index, const void* Q
                                   std::to_string((size_t)SOAR_STATIC_SCRATCH_BYTES) +
                                   "-byte static buffer; pass fewer queries per call");
     soar::select_partitions_in(index->data, Q, dtype, nq, t, top_out, score_out, static_scratch(), stream);
+  });
+}
+
+soar_status soar_check_device(void) {
+  return guarded([&] {
+    SOAR_CUDA(cudaDeviceSynchronize());
+    int* w = soar::device_error_word();
+    int v = 0;
+    SOAR_CUDA(cudaMemcpy(&v, w, sizeof(int), cudaMemcpyDeviceToHost));
+    if (v) {
+      SOAR_CUDA(cudaMemset(w, 0, sizeof(int)));
+      soar::fail(SOAR_ETIMEOUT, "a kernel gave up a bounded wait (device work of an earlier call is incomplete)");
+    }
   });
 }
 

@@ -5,6 +5,10 @@
 
 namespace soar {
 
+// A per-device int that kernels set when a bounded wait expired (api.cu);
+// soar_check_device() reads and clears it.
+int* device_error_word();
+
 // ----------------------------------------------------------- sort.cu
 
 // Exclusive prefix sum of `count` values; out may alias in.  Returns nothing;
@@ -50,6 +54,15 @@ struct IndexData {
   float* cent_code_vals = nullptr;  // [c][code_stride] decoded E4M3 code values (FP8)
   float* cent_scales = nullptr;     // [c] (FP8)
   int32_t code_stride = 0;
+  // fp32 rows for the tensor-core scan: each partition padded to 8-row groups,
+  // groups stored in the K-major core-matrix layout of tc.cuh (K = tc_kp)
+  float* tc_rows = nullptr;       // [tc_groups * 8 * tc_kp]
+  int64_t* tc_gstart = nullptr;   // [c + 1] first group of each partition
+  int32_t* tc_ids = nullptr;      // [tc_groups * 8] point id (-1 on padding)
+  float* tc_norms = nullptr;      // [tc_groups * 8] ||x|| (0 on padding)
+  float* tc_pmax = nullptr;       // [c] largest ||x|| of each partition
+  int32_t tc_kp = 0;
+  int64_t tc_groups = 0;
 };
 
 void build_index(IndexData& ix, const void* X, soar_dtype dt, const float* C, const int32_t* assign,

@@ -80,6 +80,62 @@ __global__ void size_keys(const int64_t* __restrict__ off, int c, int64_t mx, ui
   vals[p] = p;
 }
 
+__global__ void group_counts(const int64_t* __restrict__ off, int c, int64_t* __restrict__ cnt) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p > c) return;
+  cnt[p] = p < c ? (off[p + 1] - off[p] + 7) / 8 : 0;
+}
+
+// Partition p's rows -> 8-row groups in the core-matrix layout: element k of
+// padded row i goes to group gstart[p] + i/8, byte (k/4)*128 + (i%8)*16 + (k%4)*4.
+__global__ void fill_tc_rows(const float* __restrict__ rows, int row_stride, int d, const int64_t* __restrict__ off,
+                             const int32_t* __restrict__ ids, const int64_t* __restrict__ gstart, int kp,
+                             float* __restrict__ out, int32_t* __restrict__ out_ids) {
+  const int p = blockIdx.x;
+  const int64_t r0 = off[p];
+  const int size = (int)(off[p + 1] - r0);
+  const int64_t g0 = gstart[p];
+  const int padded = (int)(gstart[p + 1] - g0) * 8;
+  for (int64_t idx = threadIdx.x; idx < (int64_t)padded * kp; idx += blockDim.x) {
+    const int i = (int)(idx / kp), k = (int)(idx % kp);
+    const float v = (i < size && k < d) ? rows[(r0 + i) * row_stride + k] : 0.f;
+    out[(g0 + i / 8) * (int64_t)(8 * kp) + (k / 4) * 32 + (i % 8) * 4 + (k % 4)] = v;
+  }
+  for (int i = threadIdx.x; i < padded; i += blockDim.x) out_ids[g0 * 8 + i] = i < size ? ids[r0 + i] : -1;
+}
+
+// ||x|| of every padded row (warp per row).
+__global__ void tc_row_norms(const float* __restrict__ tc_rows, int64_t nrows_padded, int kp, float* __restrict__ norms) {
+  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r >= nrows_padded) return;
+  const float* g = tc_rows + (r / 8) * (int64_t)(8 * kp) + (r % 8) * 4;
+  float acc = 0.f;
+  for (int k = lane; k < kp; k += 32) {
+    const float v = g[(k / 4) * 32 + (k % 4)];
+    acc = fmaf(v, v, acc);
+  }
+  acc = warp_sum(acc);
+  if (lane == 0) norms[r] = sqrtf(acc);
+}
+
+// Largest row norm of every partition (block per partition).
+__global__ void partition_max_norm(const float* __restrict__ norms, const int64_t* __restrict__ gstart,
+                                   float* __restrict__ pmax) {
+  const int p = blockIdx.x;
+  float mx = 0.f;
+  for (int64_t r = gstart[p] * 8 + threadIdx.x; r < gstart[p + 1] * 8; r += blockDim.x) mx = fmaxf(mx, norms[r]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  __shared__ float wm[32];
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmaxf(mx, wm[w]);
+    pmax[p] = mx;
+  }
+}
+
 }  // namespace
 
 void quantize_fp8(const void* V, soar_dtype dt, int64_t m, int32_t d, uint8_t* codes, int32_t code_stride,
@@ -196,12 +252,37 @@ void build_index(IndexData& ix, const void* X, soar_dtype dt, const float* C, co
   SOAR_LAUNCHED();
   if (radix_sort_pairs(sk, ix.part_order, sk2, sv2, c, bits_for(mx + 1), s, scr))
     SOAR_CUDA(cudaMemcpyAsync(ix.part_order, sv2, sizeof(int32_t) * c, cudaMemcpyDeviceToDevice, s));
+
+  // fp32 indices also get the tensor-core layout of the rows
+  if (ix.mode == SOAR_SCORE_F32 && dt == SOAR_F32) {
+    ix.tc_kp = (d + 7) / 8 * 8;
+    dev_alloc((void**)&ix.tc_gstart, sizeof(int64_t) * (c + 1));
+    group_counts<<<ceil_div((int64_t)c + 1, 256), 256, 0, s>>>(ix.offsets, c, ix.tc_gstart);
+    SOAR_LAUNCHED();
+    exclusive_scan_i64(ix.tc_gstart, ix.tc_gstart, (int64_t)c + 1, s, scr);
+    int64_t groups = 0;
+    SOAR_CUDA(cudaMemcpyAsync(&groups, ix.tc_gstart + c, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SOAR_CUDA(cudaStreamSynchronize(s));
+    ix.tc_groups = groups;
+    dev_alloc((void**)&ix.tc_rows, sizeof(float) * (size_t)groups * 8 * ix.tc_kp);
+    dev_alloc((void**)&ix.tc_ids, sizeof(int32_t) * (size_t)groups * 8);
+    dev_alloc((void**)&ix.tc_norms, sizeof(float) * (size_t)groups * 8);
+    fill_tc_rows<<<c, 256, 0, s>>>(static_cast<const float*>(ix.vectors), ix.row_stride, d, ix.offsets, ix.ids,
+                                   ix.tc_gstart, ix.tc_kp, ix.tc_rows, ix.tc_ids);
+    SOAR_LAUNCHED();
+    tc_row_norms<<<ceil_div(groups * 8 * 32, 256), 256, 0, s>>>(ix.tc_rows, groups * 8, ix.tc_kp, ix.tc_norms);
+    SOAR_LAUNCHED();
+    dev_alloc((void**)&ix.tc_pmax, sizeof(float) * c);
+    partition_max_norm<<<c, 256, 0, s>>>(ix.tc_norms, ix.tc_gstart, ix.tc_pmax);
+    SOAR_LAUNCHED();
+  }
   SOAR_CUDA(cudaStreamSynchronize(s));
 }
 
 void free_index(IndexData& ix) {
   void* ptrs[] = {ix.offsets, ix.ids, ix.vectors, ix.row_scales, ix.originals, ix.centroids,
-                  ix.part_order, ix.cent_code_vals, ix.cent_scales};
+                  ix.part_order, ix.cent_code_vals, ix.cent_scales, ix.tc_rows, ix.tc_gstart,
+                  ix.tc_ids, ix.tc_norms, ix.tc_pmax};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   ix = IndexData{};

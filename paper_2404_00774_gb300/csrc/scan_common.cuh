@@ -1,0 +1,62 @@
+// Types shared by the partition-scan kernels (SIMT and tensor-core).
+#pragma once
+
+#include "internal.cuh"
+
+namespace soar {
+
+// One candidate of a per-query top-k list.
+struct Cand {
+  float s;
+  int32_t id;
+};
+
+// Order of the top-k lists: higher score first, lower id first on ties
+// (id -1, the empty slot, loses every tie).
+__device__ __forceinline__ bool better(float a, int ia, float b, int ib) {
+  return a > b || (a == b && (unsigned)ia < (unsigned)ib);
+}
+
+// Work items of the batched IVF scan: (partition, chunk of <= qb of the
+// (query, probe) pairs that probe it), partitions visited in `order`
+// (largest first).  Pairs are sorted by partition; pair e belongs to query
+// pair_vals[e] / tmax and writes its list to slot e.
+struct IvfWork {
+  const int64_t* part_off;
+  const int64_t* pair_off;
+  const int32_t* pair_vals;
+  const int32_t* order;
+  const int32_t* item_base;   // [c + 1], item_base[c] = total
+  int c, tmax, qb;
+  __device__ int count() const { return item_base[c]; }
+  __device__ int partition_of(int item) const {
+    int lo = 0, hi = c - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (item_base[mid] <= item) lo = mid; else hi = mid - 1;
+    }
+    return lo;   // index into `order`
+  }
+  __device__ void describe(int item, int64_t& r0, int64_t& r1, int64_t& e0, int& nqi) const {
+    const int lo = partition_of(item);
+    const int p = order[lo];
+    e0 = pair_off[p] + (int64_t)(item - item_base[lo]) * qb;
+    nqi = (int)min((int64_t)qb, pair_off[p + 1] - e0);
+    r0 = part_off[p];
+    r1 = part_off[p + 1];
+  }
+  __device__ int64_t query(int64_t e) const { return pair_vals[e] / tmax; }
+  __device__ int64_t slot(int64_t e) const { return e; }
+};
+
+// Tensor-core scan (scan_tc.cu) of a fp32 index (rows in the core-matrix
+// layout of tc.cuh, queries as fp32 rows of tc_kp columns): screening on the
+// tensor cores, then exact rescoring; leaves in `lists` one list of
+// scan_tc_list_len() (exact score, id) entries per pair slot, best first.
+void scan_tc_search(const IndexData& ix, const IvfWork& work, int max_items, const float* Qf, const float* qnorm,
+                    const int32_t* top, const int32_t* inv, const int32_t* tpq, int64_t nq, int t, int k,
+                    Cand* lists, int* err, cudaStream_t s, Scratch& scr);
+int scan_tc_max_k(const IndexData& ix);
+constexpr int scan_tc_list_len() { return 32; }
+
+}  // namespace soar

@@ -1,0 +1,508 @@
+// Batched IVF partition scan on the 5th-generation tensor cores (tcgen05).
+//
+// One persistent CTA per SM takes work items (partition p, up to 128 of the
+// queries that probe p).  The item's queries form the A operand (M = 128,
+// fp32 rows in shared memory, K-major core-matrix layout); the partition's
+// rows stream through a 4-stage shared-memory ring as B tiles of 64 rows,
+// copied by cp.async.bulk straight from the index, which stores every
+// partition in that same layout.  Per tile one thread issues K/8
+// tcgen05.mma (kind::tf32) into one of two TMEM accumulators (128 lanes x
+// 64 columns); four epilogue warps read the scores back (lane = query).
+//
+// Screening.  kind::tf32 truncates each fp32 operand to 10 mantissa bits,
+// so a screened score s~ lies within 2^-9 ||q|| ||x|| of the fp32 dot
+// product (fp32 accumulation error is far below that).  Per work item the
+// kernel uses one bound delta = 2^-8 ||q|| max_p ||x|| (max over the
+// partition's rows: a factor-2 margin).  Per (query, partition) it keeps
+//   * the k best screened scores; with a_k the k-th of them,
+//     L_k = a_k - delta bounds the partition's k-th best exact score from
+//     below, and
+//   * the rows with s~ + delta >= L_k (up to kCand, pruned as a_k rises);
+//     a row outside that set cannot be in the top k.
+// No row is rescored here.  rescore_lists() later takes, per query, the
+// largest L_k over its partitions, rescores exactly the candidates whose
+// upper bound reaches it and rescans exactly any partition whose candidate
+// list overflowed, so the final lists equal those of an exact scan.
+//
+// Warp roles: 0 = bulk-copy producer, 1 = TMEM owner and MMA issuer,
+// 2..5 = epilogue (query slot = 32 * (warp % 4) + lane, its TMEM lane).
+// Every mbarrier wait is bounded (about a second); on expiry the CTA raises
+// *err, stops taking work, waits (bounded) for its copies and MMAs in flight,
+// frees its TMEM and returns.
+#include "scan_common.cuh"
+#include "tc.cuh"
+
+namespace soar {
+
+namespace {
+
+constexpr int kM = 128;        // query slots per item (MMA M)
+constexpr int kN = 64;         // rows per tile (MMA N)
+constexpr int kThreads = 192;  // 6 warps
+constexpr int kMaxStages = 4;
+constexpr int kCand = 32;      // candidate rows kept per (query, partition)
+
+struct TcParams {
+  IvfWork work;
+  const float* rows;       // index rows, core-matrix layout, 8-row groups
+  const int64_t* gstart;   // [c + 1] first 8-row group of each partition
+  const float* pmax;       // [c] largest ||x|| of each partition
+  const float* Qf;         // [nq][kp] fp32 query rows
+  const float* qnorm;      // [nq]
+  int kp;                  // K, a multiple of 8
+  int k;                   // list length
+  int stages;
+  int* counter;            // work-item counter
+  int* err;                // set to 1 when a wait expired
+  Cand* cand;              // [pairs][kCand] (ub, padded row) candidates
+  int2* hdr;               // [pairs] (L_k as float bits, count | overflow << 31)
+};
+
+template <int KMAX>
+__global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // 1024-byte aligned carve-up of the dynamic shared memory
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int kp = P.kp, k = P.k, S = P.stages;
+  const uint32_t sbo = (uint32_t)kp * 32u;            // bytes between 8-row groups
+  const uint32_t a_bytes = (uint32_t)kM * kp * 4u;
+  const uint32_t b_bytes = (uint32_t)kN * kp * 4u;
+  float* sA = reinterpret_cast<float*>(base);
+  float* sB = reinterpret_cast<float*>(base + a_bytes);
+  float* av_s = reinterpret_cast<float*>(base + a_bytes + (size_t)S * b_bytes);  // [kN][kM] tile scores
+  // per-slot arrays are interleaved slot-fastest ([entry][kM]) so that the 32
+  // lanes of a warp always touch 32 distinct banks
+  float* cub_s = av_s + kN * kM;                      // [kCand][kM] candidate scores
+  int32_t* cpos_s = reinterpret_cast<int32_t*>(cub_s + kM * kCand);  // [kCand][kM] padded rows
+  uint64_t* bars = reinterpret_cast<uint64_t*>(cpos_s + kM * kCand);
+  // bars: full[S], empty[S], tfull[2], tempty[2]
+  __shared__ uint32_t tmem_base_s;
+  __shared__ int item_s;
+  __shared__ int abort_s;
+  __shared__ int issued_s, consumed_s, mma_issued_s;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  auto full = [&](int s) { return tc::smem_u32(&bars[s]); };
+  auto empty = [&](int s) { return tc::smem_u32(&bars[S + s]); };
+  auto tfull = [&](int b) { return tc::smem_u32(&bars[2 * S + b]); };
+  auto tempty = [&](int b) { return tc::smem_u32(&bars[2 * S + 2 + b]); };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      tc::bar_init(full(s), 1);
+      tc::bar_init(empty(s), 4);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::bar_init(tfull(b), 1);
+      tc::bar_init(tempty(b), 4);
+    }
+    tc::bar_init_fence();
+    abort_s = 0;
+    issued_s = consumed_s = mma_issued_s = 0;
+  }
+  if (warp == 1) tc::tmem_alloc(tc::smem_u32(&tmem_base_s), 2 * kN);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_base_s;
+  const uint32_t idesc = tc::idesc_tf32(kM, kN);
+  volatile int* abort_v = &abort_s;
+  auto give_up = [&]() {
+    if (atomicExch(&abort_s, 1) == 0) atomicExch(P.err, 1);
+  };
+
+  uint32_t tile_ctr = 0;
+  const int total = P.work.count();
+  for (;;) {
+    if (threadIdx.x == 0) item_s = abort_s ? total : atomicAdd(P.counter, 1);
+    __syncthreads();
+    const int item = item_s;
+    if (item >= total) break;
+    const int oi = P.work.partition_of(item);
+    const int p = P.work.order[oi];
+    const int64_t e0 = P.work.pair_off[p] + (int64_t)(item - P.work.item_base[oi]) * kM;
+    const int nqi = (int)min((int64_t)kM, P.work.pair_off[p + 1] - e0);
+    const int64_t row0 = P.work.part_off[p];
+    const int nrows = (int)(P.work.part_off[p + 1] - row0);
+    const int64_t g0 = P.gstart[p];
+    const int ng = (int)(P.gstart[p + 1] - g0);
+    const int ntiles = (ng + 7) / 8;
+
+    // ---- queries of the item -> A operand.  The thread owning TMEM lane m =
+    // 32 * (warp % 4) + lane takes the item's query j = 4 * lane + warp % 4,
+    // so the active queries spread evenly over the four epilogue warps.
+    const int m = 32 * (warp & 3) + lane;     // A row / TMEM lane of this thread
+    const int jq = 4 * lane + (warp & 3);     // the item's query held in that row
+    float qn = 0.f;
+    if (warp >= 2) {
+      const bool active = jq < nqi;
+      const float* q = active ? P.Qf + P.work.query(e0 + jq) * (int64_t)kp : nullptr;
+      float* arow = sA + (m >> 3) * (kp * 8) + (m & 7) * 4;
+      for (int k4 = 0; k4 < kp / 4; ++k4) {
+        float4 v = active ? *reinterpret_cast<const float4*>(q + 4 * k4) : make_float4(0.f, 0.f, 0.f, 0.f);
+        *reinterpret_cast<float4*>(arow + k4 * 32) = v;
+      }
+      if (active) qn = P.qnorm[P.work.query(e0 + jq)];
+      tc::fence_async_smem();
+    }
+    __syncthreads();
+
+    if (warp == 0) {
+      // ---- producer: one thread streams the partition's tiles
+      if (lane == 0) {
+        for (int i = 0; i < ntiles; ++i) {
+          const uint32_t T = tile_ctr + i, s = T % S, ph = (T / S) & 1;
+          if (!tc::bar_wait(empty(s), ph ^ 1, abort_v)) { give_up(); break; }
+          const int groups = min(8, ng - 8 * i);
+          const uint32_t bytes = (uint32_t)groups * 8u * kp * 4u;
+          const int64_t pr0 = (g0 + 8 * i) * 8;
+          tc::bar_arrive_expect_tx(full(s), bytes);
+          tc::bulk_copy_g2s(tc::smem_u32(sB) + s * b_bytes, P.rows + pr0 * kp, bytes, full(s));
+          issued_s = (int)(T + 1);
+        }
+      }
+    } else if (warp == 1) {
+      // ---- MMA issuer
+      if (lane == 0) {
+        for (int i = 0; i < ntiles; ++i) {
+          const uint32_t T = tile_ctr + i, s = T % S, ph = (T / S) & 1, b = T & 1, tph = (T >> 1) & 1;
+          if (!tc::bar_wait(full(s), ph, abort_v)) { give_up(); break; }
+          consumed_s = (int)(T + 1);
+          if (!tc::bar_wait(tempty(b), tph ^ 1, abort_v)) { give_up(); break; }
+          tc::fence_after_sync();
+          const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB) + s * b_bytes;
+          for (int j = 0; j < kp / 8; ++j)
+            tc::mma_tf32(tmem + b * kN, tc::smem_desc(a0 + j * 256, 128, sbo), tc::smem_desc(b0 + j * 256, 128, sbo),
+                         idesc, j > 0);
+          tc::mma_commit(tfull(b));
+          mma_issued_s = (int)(T + 1);
+        }
+      }
+    } else {
+      // ---- epilogue: screening bounds and candidate rows per query
+      const bool active = jq < nqi;
+      float ta[KMAX];                 // k best screened scores, descending (-inf until filled)
+#pragma unroll
+      for (int j = 0; j < KMAX; ++j) ta[j] = -INFINITY;
+      float* cub = cub_s + m;
+      int32_t* cpos = cpos_s + m;
+      int cnt = 0;
+      bool ovf = false;
+      const float dlt = ldexpf(qn, -8) * P.pmax[p];   // |s~ - exact| < dlt / 2 for every row of p
+      float ak = -INFINITY;                            // k-th best screened score (-inf until k seen)
+      float floor_ = -INFINITY;                        // a lower bound of the k-th best screened score
+      float cut = -INFINITY;                           // rows below cut cannot reach the top k
+      for (int i = 0; i < ntiles; ++i) {
+        const uint32_t T = tile_ctr + i, s = T % S, b = T & 1, tph = (T >> 1) & 1;
+        const bool ok = tc::bar_wait(tfull(b), tph, abort_v);
+        if (!ok) give_up();
+        tc::fence_after_sync();
+        uint32_t r0[32], r1[32];
+        const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + b * kN;
+        tc::tmem_ld32(taddr, r0);
+        tc::tmem_ld32(taddr + 32, r1);
+        tc::tmem_ld_wait();
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) tc::bar_arrive(tempty(b));
+        if (!ok) break;
+        const int nvalid = min(kN, nrows - kN * i);
+        const int32_t pr0 = (int32_t)((g0 + 8 * i) * 8);
+        if (ak == -INFINITY && k <= 16 && nvalid == kN) {
+          // the k-th largest of 16 group maxima (groups of 4 rows) is a lower
+          // bound of the tile's k-th best screened score: seed the cut with it
+          float g[16];
+#pragma unroll
+          for (int q4 = 0; q4 < 16; ++q4) {
+            const int c = 4 * q4;
+            const float a0 = __uint_as_float(c < 32 ? r0[c & 31] : r1[c & 31]);
+            const float a1 = __uint_as_float(c + 1 < 32 ? r0[(c + 1) & 31] : r1[(c + 1) & 31]);
+            const float a2 = __uint_as_float(c + 2 < 32 ? r0[(c + 2) & 31] : r1[(c + 2) & 31]);
+            const float a3 = __uint_as_float(c + 3 < 32 ? r0[(c + 3) & 31] : r1[(c + 3) & 31]);
+            g[q4] = fmaxf(fmaxf(a0, a1), fmaxf(a2, a3));
+          }
+          // bitonic sort of the 16 maxima, descending
+#pragma unroll
+          for (int size = 2; size <= 16; size <<= 1)
+#pragma unroll
+            for (int stride = size >> 1; stride > 0; stride >>= 1)
+#pragma unroll
+              for (int i2 = 0; i2 < 16; ++i2) {
+                const int j2 = i2 ^ stride;
+                if (j2 > i2) {
+                  const bool desc = (i2 & size) == 0;
+                  const float x = g[i2], y = g[j2];
+                  g[i2] = desc ? fmaxf(x, y) : fminf(x, y);
+                  g[j2] = desc ? fminf(x, y) : fmaxf(x, y);
+                }
+              }
+          float seed = g[0];
+#pragma unroll
+          for (int j2 = 0; j2 < 16; ++j2)
+            if (j2 == k - 1) seed = g[j2];
+          floor_ = seed;
+          cut = seed - 2.f * dlt;
+        }
+        // register-only screen against the cut at the tile's start (the cut
+        // only rises, so this keeps a superset); scores parked in smem
+        uint64_t mask = 0;
+#pragma unroll
+        for (int c = 0; c < kN; ++c) {
+          const float a = __uint_as_float(c < 32 ? r0[c & 31] : r1[c & 31]);
+          av_s[c * kM + m] = a;
+          mask |= (uint64_t)(c < nvalid && a >= cut) << c;
+        }
+        if (!active) mask = 0;
+        // pass 1: the tile's survivors raise the k best screened scores (registers only)
+        for (uint64_t m1 = mask; m1; m1 &= m1 - 1) {
+          const int c = __ffsll((long long)m1) - 1;
+          const float a = av_s[c * kM + m];
+          if (a > ak && a >= cut) {
+            float v = a;
+#pragma unroll
+            for (int j = 0; j < KMAX; ++j) {
+              if (j < k) {
+                const float hi = fmaxf(ta[j], v);
+                v = fminf(ta[j], v);
+                ta[j] = hi;
+              }
+            }
+#pragma unroll
+            for (int j = 0; j < KMAX; ++j)
+              if (j == k - 1) ak = ta[j];
+          }
+        }
+        cut = fmaxf(ak, floor_) - 2.f * dlt;       // s~ + dlt < ak - dlt  <=>  s~ < cut
+        // pass 2: keep the rows that survive the tile's final cut
+        for (; mask; mask &= mask - 1) {
+          const int c = __ffsll((long long)mask) - 1;
+          const float a = av_s[c * kM + m];
+          if (a < cut) continue;
+          if (cnt == kCand) {                      // drop candidates that fell below the cut
+            int w = 0;
+            for (int j = 0; j < kCand; ++j)
+              if (cub[j * kM] >= cut) { cub[w * kM] = cub[j * kM]; cpos[w * kM] = cpos[j * kM]; ++w; }
+            cnt = w;
+          }
+          if (cnt < kCand) {
+            cub[cnt * kM] = a;
+            cpos[cnt * kM] = pr0 + c;
+            ++cnt;
+          } else {
+            ovf = true;
+          }
+        }
+        __syncwarp();
+        if (lane == 0) tc::bar_arrive(empty(s));
+      }
+      if (active && !abort_s) {
+        const int64_t e = e0 + jq;
+        Cand* out = P.cand + e * kCand;
+        int w = 0;
+        for (int j = 0; j < cnt; ++j)
+          if (cub[j * kM] >= cut) out[w++] = Cand{cub[j * kM] + dlt, cpos[j * kM]};   // upper bound of the exact score
+        const float Lk = fmaxf(ak, floor_) - dlt;   // -inf while fewer than k rows were seen
+        P.hdr[e] = make_int2(__float_as_int(Lk), w | (ovf ? (int)0x80000000 : 0));
+      }
+    }
+    tile_ctr += ntiles;
+    __syncthreads();
+  }
+
+  // ---- teardown: after an abort, let copies and MMAs in flight land first
+  __syncthreads();
+  if (abort_s && threadIdx.x == 0) {
+    volatile int never = 0;
+    for (int T = consumed_s; T < issued_s; ++T) tc::bar_wait(full(T % S), (T / S) & 1, &never);
+  }
+  if (abort_s && threadIdx.x == 32 && mma_issued_s > 0) {
+    volatile int never = 0;
+    const int T = mma_issued_s - 1;
+    tc::bar_wait(tfull(T & 1), (T >> 1) & 1, &never);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 1) tc::tmem_dealloc(tmem, 2 * kN);
+}
+
+size_t smem_bytes(int kp, int k, int stages) {
+  return 1024 + (size_t)kM * kp * 4 + (size_t)stages * kN * kp * 4 + (size_t)kN * kM * 4 +
+         (size_t)kM * kCand * 8 + (size_t)(2 * stages + 4) * 8;
+}
+
+int pick_stages(int kp, int k) {
+  for (int s = kMaxStages; s >= 2; --s)
+    if (smem_bytes(kp, k, s) <= 220 * 1024) return s;
+  return 0;
+}
+
+
+// Largest L_k over each query's partitions: a lower bound of its final k-th
+// best exact score.
+__global__ void query_bounds(const int2* __restrict__ hdr, const int32_t* __restrict__ inv, int64_t nq, int t,
+                             const int32_t* __restrict__ tpq, float* __restrict__ lstar) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  const int tq = tpq ? min(max(tpq[q], 1), t) : t;
+  float best = -INFINITY;
+  for (int j = 0; j < tq; ++j) best = fmaxf(best, __int_as_float(hdr[inv[q * t + j]].x));
+  lstar[q] = best;
+}
+
+// Exact fp32 <q, x> of padded row `pos` (k ascending, one thread).
+__device__ __forceinline__ float exact_dot(const float* __restrict__ q, const float* __restrict__ rows, int kp,
+                                           int64_t pos) {
+  const float* x = rows + (pos >> 3) * (int64_t)(8 * kp) + (pos & 7) * 4;
+  float acc = 0.f;
+  for (int k4 = 0; k4 < kp / 4; ++k4) {
+    const float4 a = *reinterpret_cast<const float4*>(q + 4 * k4);
+    const float4 v = __ldg(reinterpret_cast<const float4*>(x + k4 * 32));
+    acc = fmaf(a.x, v.x, acc);
+    acc = fmaf(a.y, v.y, acc);
+    acc = fmaf(a.z, v.z, acc);
+    acc = fmaf(a.w, v.w, acc);
+  }
+  return acc;
+}
+
+// Warp per (query, partition) slot: the candidates whose upper bound reaches
+// the query's bound are rescored exactly; a slot whose list overflowed is
+// rescanned exactly over its whole partition (its exact top-k kept).  The
+// slot is rewritten as a list of (exact score, id), best first, padded with
+// (-inf, -1).
+__global__ void __launch_bounds__(256) rescore_lists(Cand* __restrict__ cand, const int2* __restrict__ hdr,
+                                                     int64_t P, const int32_t* __restrict__ pair_vals, int t,
+                                                     const float* __restrict__ lstar, const float* __restrict__ Qf,
+                                                     int kp, const float* __restrict__ rows,
+                                                     const int32_t* __restrict__ ids,
+                                                     const int32_t* __restrict__ part_of_pair,
+                                                     const int64_t* __restrict__ gstart,
+                                                     const int64_t* __restrict__ part_off, int k,
+                                                     const int32_t* __restrict__ tpq) {
+  const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (e >= P) return;
+  const int64_t q = pair_vals[e] / t;
+  const int j = pair_vals[e] - (int)(q * t);
+  if (tpq && j >= min(max(tpq[q], 1), t)) return;   // a probe beyond the query's own t: no list
+  const int2 h = hdr[e];
+  const int cnt = h.y & 0x7fffffff;
+  const bool ovf = h.y < 0;
+  const float bound = lstar[q];
+  const float* qv = Qf + q * (int64_t)kp;
+  Cand* slot = cand + e * kCand;
+  float s = -INFINITY;
+  int id = -1;
+  if (!ovf) {
+    if (lane < cnt) {
+      const Cand c = slot[lane];
+      if (c.s >= bound) {
+        s = exact_dot(qv, rows, kp, c.id);
+        id = ids[c.id];
+      }
+    }
+  } else {
+    // exact rescan of the partition; each lane keeps the best of its rows,
+    // then the warp keeps the k best overall (k <= 32)
+    const int p = part_of_pair[e];
+    const int64_t r0 = gstart[p] * 8;
+    const int64_t nrows = part_off[p + 1] - part_off[p];
+    Cand mine[kCand];
+    int have = 0;
+    for (int64_t r = lane; r < nrows; r += 32) {
+      const float v = exact_dot(qv, rows, kp, r0 + r);
+      const int rid = ids[r0 + r];
+      if (have < k || better(v, rid, mine[have - 1].s, mine[have - 1].id)) {
+        int pos = have < k ? have : k - 1;
+        while (pos > 0 && better(v, rid, mine[pos - 1].s, mine[pos - 1].id)) {
+          mine[pos] = mine[pos - 1];
+          --pos;
+        }
+        mine[pos] = Cand{v, rid};
+        if (have < k) ++have;
+      }
+    }
+    int head = 0;
+    for (int out = 0; out < k; ++out) {
+      float bs = head < have ? mine[head].s : -INFINITY;
+      int bid = head < have ? mine[head].id : -1;
+      int wl = head < have ? lane : 32;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float os = __shfl_xor_sync(0xffffffffu, bs, o);
+        const int oid = __shfl_xor_sync(0xffffffffu, bid, o);
+        const int ol = __shfl_xor_sync(0xffffffffu, wl, o);
+        if (ol != 32 && (wl == 32 || better(os, oid, bs, bid))) { bs = os; bid = oid; wl = ol; }
+      }
+      if (lane == out) { s = bs; id = wl == 32 ? -1 : bid; }
+      if (wl != 32 && lane == wl) ++head;
+    }
+  }
+  // bitonic sort of the 32 lane values, best first
+#pragma unroll
+  for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      const float os = __shfl_xor_sync(0xffffffffu, s, stride);
+      const int oid = __shfl_xor_sync(0xffffffffu, id, stride);
+      const bool up = (lane & size) == 0;          // this 'size' block sorts best-first
+      const bool lower = (lane & stride) == 0;
+      const bool other_better = better(os, oid, s, id);
+      const bool take = (lower == up) ? other_better : (!other_better && !(os == s && oid == id));
+      if (take) { s = os; id = oid; }
+    }
+  }
+  slot[lane] = Cand{s, id};
+}
+
+// partition of every sorted pair (for the overflow rescans)
+__global__ void pair_partitions(const int32_t* __restrict__ top, const int32_t* __restrict__ pair_vals, int64_t P,
+                                int32_t* __restrict__ part) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < P) part[e] = top[pair_vals[e]];
+}
+
+}  // namespace
+
+int scan_tc_max_k(const IndexData& ix) {
+  int k = 0;
+  while (k < kCand && pick_stages(ix.tc_kp, k + 1) >= 2) ++k;
+  return k;
+}
+
+void scan_tc_search(const IndexData& ix, const IvfWork& work, int max_items, const float* Qf, const float* qnorm,
+                    const int32_t* top, const int32_t* inv, const int32_t* tpq, int64_t nq, int t, int k,
+                    Cand* lists, int* err, cudaStream_t s, Scratch& scr) {
+  const int stages = pick_stages(ix.tc_kp, k);
+  if (stages < 2 || k > kCand) fail(SOAR_EUNSUPPORTED, "tensor-core scan: k too large");
+  const int64_t P = nq * t;
+  int2* hdr = scr.get<int2>(P);
+  TcParams prm{work, ix.tc_rows, ix.tc_gstart, ix.tc_pmax, Qf, qnorm, ix.tc_kp, k, stages,
+               nullptr, err, lists, hdr};
+  prm.counter = scr.get<int>(1);
+  SOAR_CUDA(cudaMemsetAsync(prm.counter, 0, sizeof(int), s));
+  const size_t smem = smem_bytes(ix.tc_kp, k, stages);
+  auto kern = k <= 16 ? scan_tc_kernel<16> : scan_tc_kernel<32>;
+  SOAR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int grid = std::max(1, std::min(max_items, num_sms()));
+  stage_mark(s, "scan", true);
+  kern<<<grid, kThreads, smem, s>>>(prm);
+  SOAR_LAUNCHED();
+  stage_mark(s, "scan", false);
+  stage_mark(s, "rescore", true);
+  float* lstar = scr.get<float>(nq);
+  query_bounds<<<ceil_div(nq, 256), 256, 0, s>>>(hdr, inv, nq, t, tpq, lstar);
+  SOAR_LAUNCHED();
+  int32_t* part = scr.get<int32_t>(P);
+  pair_partitions<<<ceil_div(P, 256), 256, 0, s>>>(top, work.pair_vals, P, part);
+  SOAR_LAUNCHED();
+  rescore_lists<<<ceil_div(P * 32, 256), 256, 0, s>>>(lists, hdr, P, work.pair_vals, t, lstar, Qf, ix.tc_kp,
+                                                      ix.tc_rows, ix.tc_ids, part, ix.tc_gstart, ix.offsets, k,
+                                                      tpq);
+  SOAR_LAUNCHED();
+  stage_mark(s, "rescore", false);
+}
+
+}  // namespace soar

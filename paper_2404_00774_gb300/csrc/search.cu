@@ -20,6 +20,7 @@
 #include <algorithm>
 
 #include "internal.cuh"
+#include "scan_common.cuh"
 
 namespace soar {
 
@@ -29,15 +30,6 @@ constexpr int QB = 64;          // query slots per work item
 constexpr int RB = 64;          // rows per tile
 constexpr int SSTRIDE = RB + 4; // score tile stride (conflict-free epilogue reads)
 constexpr int kThreads = 256;
-
-struct Cand {
-  float s;
-  int32_t id;
-};
-
-__device__ __forceinline__ bool better(float a, int ia, float b, int ib) {
-  return a > b || (a == b && (unsigned)ia < (unsigned)ib);
-}
 
 // smem row stride (floats) for a row of `row_stride` elements: >= row_stride,
 // a multiple of 4, and == 4 (mod 32) so 8 consecutive rows read by float4
@@ -285,30 +277,6 @@ __global__ void item_counts(const int64_t* __restrict__ pair_off, const int32_t*
 }
 
 // ------------------------------------------------------------ scan
-
-struct IvfWork {
-  const int64_t* part_off;
-  const int64_t* pair_off;
-  const int32_t* pair_vals;
-  const int32_t* order;
-  const int32_t* item_base;   // [c + 1], item_base[c] = total
-  int c, tmax, qb;
-  __device__ int count() const { return item_base[c]; }
-  __device__ void describe(int item, int64_t& r0, int64_t& r1, int64_t& e0, int& nqi) const {
-    int lo = 0, hi = c - 1;
-    while (lo < hi) {
-      int mid = (lo + hi + 1) >> 1;
-      if (item_base[mid] <= item) lo = mid; else hi = mid - 1;
-    }
-    int p = order[lo];
-    e0 = pair_off[p] + (int64_t)(item - item_base[lo]) * qb;
-    nqi = (int)min((int64_t)qb, pair_off[p + 1] - e0);
-    r0 = part_off[p];
-    r1 = part_off[p + 1];
-  }
-  __device__ int64_t query(int64_t e) const { return pair_vals[e] / tmax; }
-  __device__ int64_t slot(int64_t e) const { return e; }
-};
 
 struct BruteWork {
   int64_t n, nq, rb;
@@ -670,10 +638,18 @@ void select_prepared(const IndexData& ix, const float* Qf, const float* qscale, 
   SOAR_LAUNCHED();
 }
 
-template <typename RowT>
-void ivf_scan_typed(const IndexData& ix, const float* Qf, const float* qscale, int64_t nq, int t,
-                    const int32_t* tpq, int len, Cand* partials, int32_t* inv, const int32_t* top,
-                    cudaStream_t s, Scratch& scr) {
+struct Grouped {
+  int64_t* pair_off;       // [c + 1]
+  const int32_t* vals;     // pairs sorted by partition (value q * t + j)
+  int32_t* item_base;      // [c + 1]
+  int max_items;
+};
+
+// (query, probe) pairs sorted by partition with a stable radix sort, the
+// inverse map inv[q * t + j] = sorted position, and the work items
+// (partition, <= qb pairs) counted over partitions in size order.
+Grouped group_pairs(const IndexData& ix, int64_t nq, int t, const int32_t* tpq, int qb, const int32_t* top,
+                    int32_t* inv, cudaStream_t s, Scratch& scr) {
   const int64_t P = nq * t;
   uint32_t* keys = scr.get<uint32_t>(P);
   int32_t* vals = scr.get<int32_t>(P);
@@ -685,20 +661,44 @@ void ivf_scan_typed(const IndexData& ix, const float* Qf, const float* qscale, i
   bool in_tmp = radix_sort_pairs(keys, vals, keys2, vals2, P, bits_for((int64_t)ix.c + 1), s, scr);
   const uint32_t* ks = in_tmp ? keys2 : keys;
   const int32_t* vs = in_tmp ? vals2 : vals;
-  int64_t* pair_off = scr.get<int64_t>((size_t)ix.c + 1);
-  segment_offsets(ks, P, ix.c, pair_off, s);
+  Grouped g;
+  g.pair_off = scr.get<int64_t>((size_t)ix.c + 1);
+  segment_offsets(ks, P, ix.c, g.pair_off, s);
   invert_pairs<<<ceil_div(P, 256), 256, 0, s>>>(vs, P, inv);
   SOAR_LAUNCHED();
-  const int qb = scan_qb(scan_xs<RowT>(ix.row_stride), len);
-  int32_t* item_base = scr.get<int32_t>((size_t)ix.c + 1);
-  item_counts<<<ceil_div((int64_t)ix.c + 1, 256), 256, 0, s>>>(pair_off, ix.part_order, ix.c, qb, item_base);
+  g.item_base = scr.get<int32_t>((size_t)ix.c + 1);
+  item_counts<<<ceil_div((int64_t)ix.c + 1, 256), 256, 0, s>>>(g.pair_off, ix.part_order, ix.c, qb, g.item_base);
   SOAR_LAUNCHED();
-  exclusive_scan_i32(item_base, item_base, (int64_t)ix.c + 1, s, scr);
-  IvfWork work{ix.offsets, pair_off, vs, ix.part_order, item_base, ix.c, t, qb};
-  const int max_items = (int)std::min<int64_t>(P / qb + ix.c + 1, 1 << 30);
+  exclusive_scan_i32(g.item_base, g.item_base, (int64_t)ix.c + 1, s, scr);
   stage_mark(s, "group", false);
-  launch_scan<RowT, IvfWork>(work, 1, max_items, static_cast<const RowT*>(ix.vectors), ix.row_stride, ix.ids,
+  g.vals = vs;
+  g.max_items = (int)std::min<int64_t>(P / qb + ix.c + 1, 1 << 30);
+  return g;
+}
+
+template <typename RowT>
+void ivf_scan_typed(const IndexData& ix, const float* Qf, const float* qscale, int64_t nq, int t,
+                    const int32_t* tpq, int len, Cand* partials, int32_t* inv, const int32_t* top,
+                    cudaStream_t s, Scratch& scr) {
+  const int qb = scan_qb(scan_xs<RowT>(ix.row_stride), len);
+  Grouped g = group_pairs(ix, nq, t, tpq, qb, top, inv, s, scr);
+  IvfWork work{ix.offsets, g.pair_off, g.vals, ix.part_order, g.item_base, ix.c, t, qb};
+  launch_scan<RowT, IvfWork>(work, 1, g.max_items, static_cast<const RowT*>(ix.vectors), ix.row_stride, ix.ids,
                              ix.row_scales, Qf, qscale, len, qb, partials, s, scr);
+}
+
+// ||q|| of every prepared query row (warp per query).
+__global__ void query_norms(const float* __restrict__ Qf, int64_t nq, int stride, float* __restrict__ qn) {
+  const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (q >= nq) return;
+  float acc = 0.f;
+  for (int k = lane; k < stride; k += 32) {
+    const float v = Qf[q * stride + k];
+    acc = fmaf(v, v, acc);
+  }
+  acc = warp_sum(acc);
+  if (lane == 0) qn[q] = sqrtf(acc);
 }
 
 }  // namespace
@@ -750,6 +750,34 @@ void search(const IndexData& ix, const void* Q, soar_dtype dt, int64_t nq, int32
             const int32_t* tpq, int32_t rescore, int64_t* ids_out, float* scores_out, cudaStream_t s,
             Scratch& scr) {
   const bool fp8 = ix.mode == SOAR_SCORE_FP8;
+  if (!fp8 && ix.tc_rows && k <= scan_tc_max_k(ix)) {
+    // fp32 index: tensor-core screening with exact fp32 rescoring
+    const int qstride = ix.tc_kp;
+    float* Qf = scr.get<float>((size_t)nq * qstride);
+    float* qn = scr.get<float>(nq);
+    stage_mark(s, "select", true);
+    prep_any(Q, dt, nq, ix.d, qstride, false, Qf, nullptr, s);
+    query_norms<<<ceil_div(nq * 32, 256), 256, 0, s>>>(Qf, nq, qstride, qn);
+    SOAR_LAUNCHED();
+    int32_t* top = scr.get<int32_t>((size_t)nq * t);
+    select_prepared(ix, Qf, nullptr, nq, qstride, t, top, nullptr, s, scr);
+    stage_mark(s, "select", false);
+    const int64_t P = nq * t;
+    int32_t* inv = scr.get<int32_t>(P);
+    const int len = scan_tc_list_len();
+    Cand* lists = scr.get<Cand>((size_t)P * len);
+    Grouped g = group_pairs(ix, nq, t, tpq, 128, top, inv, s, scr);
+    IvfWork work{ix.offsets, g.pair_off, g.vals, ix.part_order, g.item_base, ix.c, t, 128};
+    scan_tc_search(ix, work, g.max_items, Qf, qn, top, inv, tpq, nq, t, k, lists, device_error_word(), s, scr);
+    const int smem = 4 * t * (int)sizeof(uint16_t);
+    SOAR_CUDA(cudaFuncSetAttribute(merge_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    stage_mark(s, "merge", true);
+    merge_kernel<true><<<ceil_div(nq, 4), 128, smem, s>>>(lists, len, nq, t, tpq, inv, 0, k, ids_out, nullptr,
+                                                          scores_out);
+    SOAR_LAUNCHED();
+    stage_mark(s, "merge", false);
+    return;
+  }
   // query rows padded exactly like the index rows (float elements)
   int qstride;
   if (fp8) qstride = ix.code_stride;

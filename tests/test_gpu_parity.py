@@ -210,6 +210,31 @@ def test_search_pads_when_candidates_run_out(soar):
     ix.close()
 
 
+def test_search_equal_rows_overflow_candidate_lists(soar):
+    # 48 identical rows in one partition tie exactly for queries sitting on
+    # them: more candidates than a screened list holds, so the exact rescan of
+    # that partition decides, and ties must still go to the lower ids
+    rng = np.random.default_rng(31)
+    X = rng.standard_normal((3000, 40)).astype(np.float32)
+    X /= np.linalg.norm(X, axis=1, keepdims=True)
+    X[100:148] = X[100]
+    Q = rng.standard_normal((20, 40)).astype(np.float32)
+    Q[:6] = X[100] + 0.01 * rng.standard_normal((6, 40)).astype(np.float32)
+    Q /= np.linalg.norm(Q, axis=1, keepdims=True)
+    C = oracle.kmeans(X, rng.choice(3000, 16, replace=False), 3)
+    A = oracle.soar_assign(X, C, 1.0, 1)
+    off, ids = oracle.build_ivf(A, 16)
+    ix = soar.soar_index_build(_t(X), _t(C), _t(A))
+    for k, t in [(10, 2), (32, 3), (1, 1)]:
+        gi, gs = soar.soar_search(ix, _t(Q), k, t)
+        wi, ws = oracle.ivf_search(Q, X, C, off, ids, k, t)
+        gi = gi.cpu().numpy()
+        assert topk_mismatches(gi, wi, ws, _exact(X, Q)) == [], (k, t)
+        np.testing.assert_array_equal(gi[:6, :min(k, 10)], wi[:6, :min(k, 10)])
+    soar.soar_check_device()
+    ix.close()
+
+
 def test_search_bf16_index(soar, tiny):
     X, Q, init, C = tiny
     Xb = oracle.bf16_round(X)
