@@ -54,9 +54,18 @@ struct TcParams {
   int stages;
   int* counter;            // work-item counter
   int* err;                // set to 1 when a wait expired
+  unsigned* gbound;        // [nq] per-query lower bound of the final k-th best exact score (ordered key)
   Cand* cand;              // [pairs][kCand] (ub, padded row) candidates
   int2* hdr;               // [pairs] (L_k as float bits, count | overflow << 31)
 };
+
+__device__ __forceinline__ unsigned ordered(float f) {
+  const unsigned u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float unordered(unsigned k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
 
 template <int KMAX>
 __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
@@ -190,9 +199,13 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
       int cnt = 0;
       bool ovf = false;
       const float dlt = ldexpf(qn, -8) * P.pmax[p];   // |s~ - exact| < dlt / 2 for every row of p
+      // G_q, published by this query's finished partitions, bounds its final
+      // k-th best exact score from below: rows with s~ + dlt < G_q cannot count
+      const int64_t qid = active ? P.work.query(e0 + jq) : 0;
+      float gq = active ? unordered(__ldcg(P.gbound + qid)) - dlt : -INFINITY;
       float ak = -INFINITY;                            // k-th best screened score (-inf until k seen)
       float floor_ = -INFINITY;                        // a lower bound of the k-th best screened score
-      float cut = -INFINITY;                           // rows below cut cannot reach the top k
+      float cut = gq;                                  // rows below cut cannot reach the top k
       for (int i = 0; i < ntiles; ++i) {
         const uint32_t T = tile_ctr + i, s = T % S, b = T & 1, tph = (T >> 1) & 1;
         const bool ok = tc::bar_wait(tfull(b), tph, abort_v);
@@ -242,7 +255,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
           for (int j2 = 0; j2 < 16; ++j2)
             if (j2 == k - 1) seed = g[j2];
           floor_ = seed;
-          cut = seed - 2.f * dlt;
+          cut = fmaxf(seed - 2.f * dlt, gq);
         }
         // register-only screen against the cut at the tile's start (the cut
         // only rises, so this keeps a superset); scores parked in smem
@@ -273,7 +286,8 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
               if (j == k - 1) ak = ta[j];
           }
         }
-        cut = fmaxf(ak, floor_) - 2.f * dlt;       // s~ + dlt < ak - dlt  <=>  s~ < cut
+        if (active && (i & 3) == 3) gq = fmaxf(gq, unordered(__ldcg(P.gbound + qid)) - dlt);
+        cut = fmaxf(fmaxf(ak, floor_) - 2.f * dlt, gq);   // s~ + dlt < max(L_k, G_q)  <=>  s~ < cut
         // pass 2: keep the rows that survive the tile's final cut
         for (; mask; mask &= mask - 1) {
           const int c = __ffsll((long long)mask) - 1;
@@ -304,6 +318,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
           if (cub[j * kM] >= cut) out[w++] = Cand{cub[j * kM] + dlt, cpos[j * kM]};   // upper bound of the exact score
         const float Lk = fmaxf(ak, floor_) - dlt;   // -inf while fewer than k rows were seen
         P.hdr[e] = make_int2(__float_as_int(Lk), w | (ovf ? (int)0x80000000 : 0));
+        if (Lk > -INFINITY) atomicMax(P.gbound + qid, ordered(Lk));
       }
     }
     tile_ctr += ntiles;
@@ -457,6 +472,11 @@ __global__ void __launch_bounds__(256) rescore_lists(Cand* __restrict__ cand, co
   slot[lane] = Cand{s, id};
 }
 
+__global__ void fill_u32(unsigned* __restrict__ a, int64_t n, unsigned v) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = v;
+}
+
 // partition of every sorted pair (for the overflow rescans)
 __global__ void pair_partitions(const int32_t* __restrict__ top, const int32_t* __restrict__ pair_vals, int64_t P,
                                 int32_t* __restrict__ part) {
@@ -480,7 +500,10 @@ void scan_tc_search(const IndexData& ix, const IvfWork& work, int max_items, con
   const int64_t P = nq * t;
   int2* hdr = scr.get<int2>(P);
   TcParams prm{work, ix.tc_rows, ix.tc_gstart, ix.tc_pmax, Qf, qnorm, ix.tc_kp, k, stages,
-               nullptr, err, lists, hdr};
+               nullptr, err, nullptr, lists, hdr};
+  prm.gbound = scr.get<unsigned>(nq);
+  fill_u32<<<ceil_div(nq, 256), 256, 0, s>>>(prm.gbound, nq, 0x007fffffu);   // ordered key of -inf
+  SOAR_LAUNCHED();
   prm.counter = scr.get<int>(1);
   SOAR_CUDA(cudaMemsetAsync(prm.counter, 0, sizeof(int), s));
   const size_t smem = smem_bytes(ix.tc_kp, k, stages);

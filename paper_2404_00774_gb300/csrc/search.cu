@@ -155,10 +155,89 @@ __global__ void __launch_bounds__(256) gemm_nt(const float* __restrict__ A, int6
   }
 }
 
+// Tiled fp32 GEMM S = A . B^T (same contract as gemm_nt) for 16-byte aligned
+// rows: 128 x 128 block tile, 8 x 8 outputs per thread, K in steps of 8 with
+// the next step prefetched into registers while the current one computes.
+__global__ void __launch_bounds__(256) gemm_nt_128(const float* __restrict__ A, int64_t m, int lda,
+                                                   const float* __restrict__ B, int nb, int ldb, int d,
+                                                   const float* __restrict__ ascale,
+                                                   const float* __restrict__ bscale, float* __restrict__ S) {
+  constexpr int TB = 128, TK = 8;
+  __shared__ __align__(16) float As[2][TK][TB];
+  __shared__ __align__(16) float Bs[2][TK][TB];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int64_t m0 = (int64_t)blockIdx.y * TB;
+  const int n0 = blockIdx.x * TB;
+  // loader: thread -> (row lr, k-quad lq) of a 128 x 8 tile, one float4 each for A and B
+  const int lr = tid >> 1, lq = (tid & 1) * 4;
+  const bool arow = m0 + lr < m, brow = n0 + lr < nb;
+  const float* ap = A + (m0 + lr) * (int64_t)lda;
+  const float* bp = B + (int64_t)(n0 + lr) * ldb;
+  auto load = [&](int k0, float4& va, float4& vb) {
+    const int k = k0 + lq;
+    va = (arow && k < d) ? *reinterpret_cast<const float4*>(ap + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+    vb = (brow && k < d) ? *reinterpret_cast<const float4*>(bp + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+    // columns k+1..k+3 beyond d are zero in A's padded rows; B rows are read to
+    // the next multiple of 4, so clear them explicitly
+    if (k + 3 >= d) {
+      if (k + 1 >= d) { va.y = 0.f; vb.y = 0.f; }
+      if (k + 2 >= d) { va.z = 0.f; vb.z = 0.f; }
+      if (k + 3 >= d) { va.w = 0.f; vb.w = 0.f; }
+    }
+  };
+  auto store = [&](int buf, const float4& va, const float4& vb) {
+    As[buf][lq + 0][lr] = va.x; As[buf][lq + 1][lr] = va.y; As[buf][lq + 2][lr] = va.z; As[buf][lq + 3][lr] = va.w;
+    Bs[buf][lq + 0][lr] = vb.x; Bs[buf][lq + 1][lr] = vb.y; Bs[buf][lq + 2][lr] = vb.z; Bs[buf][lq + 3][lr] = vb.w;
+  };
+  float acc[8][8] = {};
+  float4 va, vb;
+  load(0, va, vb);
+  store(0, va, vb);
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = 0; k0 < d; k0 += TK) {
+    const bool more = k0 + TK < d;
+    if (more) load(k0 + TK, va, vb);
+#pragma unroll
+    for (int kk = 0; kk < TK; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][64 + ty * 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][64 + tx * 4]);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+    if (more) {
+      store(buf ^ 1, va, vb);
+      __syncthreads();
+      buf ^= 1;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int64_t r = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+    if (r >= m) continue;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int col = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
+      if (col >= nb) continue;
+      float v = acc[i][j];
+      if (ascale) v = v * ascale[r] * bscale[col];
+      S[r * nb + col] = v;
+    }
+  }
+}
+
 // ------------------------------------------------------------ top-t select
 
 // One block per row of S: the t best columns (score desc, lower id on ties),
-// sorted.  Dynamic smem: pow2 >= t 64-bit keys.
+// sorted.  Dynamic smem: pow2 >= t 64-bit keys, then the row itself when
+// c <= kToptSmemRow.
+constexpr int kToptSmemRow = 12288;
 __global__ void __launch_bounds__(256) topt_kernel(const float* __restrict__ S, int c, int t, int t2,
                                                    int32_t* __restrict__ top, float* __restrict__ top_s) {
   extern __shared__ uint64_t buf[];
@@ -170,6 +249,13 @@ __global__ void __launch_bounds__(256) topt_kernel(const float* __restrict__ S, 
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int64_t q = blockIdx.x;
   const float* row = S + q * c;
+  if (c <= kToptSmemRow) {
+    // the row is read four times: keep it in shared memory behind the sort buffer
+    float* srow = reinterpret_cast<float*>(buf + t2);
+    for (int i = tid; i < c; i += 256) srow[i] = row[i];
+    __syncthreads();
+    row = srow;
+  }
   uint32_t prefix = 0;
   int remaining = t;
   for (int pass = 0; pass < 4; ++pass) {
@@ -621,18 +707,33 @@ int pow2_at_least(int v) {
   return p;
 }
 
+// S = Q . C^T for prepared queries (FP8 indices: scaled code products).
+void score_centroids(const IndexData& ix, const float* Qf, const float* qscale, int64_t nq, int qstride, float* S,
+                     cudaStream_t s) {
+  const bool fp8 = ix.mode == SOAR_SCORE_FP8;
+  const float* B = fp8 ? ix.cent_code_vals : ix.centroids;
+  const int ldb = fp8 ? ix.code_stride : ix.d;
+  const bool aligned = qstride % 4 == 0 && ldb % 4 == 0 && (reinterpret_cast<uintptr_t>(Qf) & 15u) == 0 &&
+                       (reinterpret_cast<uintptr_t>(B) & 15u) == 0;
+  if (aligned) {
+    dim3 grid(ceil_div(ix.c, 128), ceil_div(nq, 128));
+    gemm_nt_128<<<grid, 256, 0, s>>>(Qf, nq, qstride, B, ix.c, ldb, ix.d, fp8 ? qscale : nullptr,
+                                     fp8 ? ix.cent_scales : nullptr, S);
+  } else {
+    dim3 grid(ceil_div(ix.c, 64), ceil_div(nq, 64));
+    gemm_nt<<<grid, 256, 0, s>>>(Qf, nq, qstride, B, ix.c, ldb, ix.d, fp8 ? qscale : nullptr,
+                                 fp8 ? ix.cent_scales : nullptr, S);
+  }
+  SOAR_LAUNCHED();
+}
+
 // Queries already prepared (Qf, row stride qstride); writes top [nq][t].
 void select_prepared(const IndexData& ix, const float* Qf, const float* qscale, int64_t nq, int qstride, int t,
                      int32_t* top, float* top_s, cudaStream_t s, Scratch& scr) {
   float* S = scr.get<float>((size_t)nq * ix.c);
-  dim3 grid(ceil_div(ix.c, 64), ceil_div(nq, 64));
-  const bool fp8 = ix.mode == SOAR_SCORE_FP8;
-  gemm_nt<<<grid, 256, 0, s>>>(Qf, nq, qstride, fp8 ? ix.cent_code_vals : ix.centroids, ix.c,
-                               fp8 ? ix.code_stride : ix.d, ix.d, fp8 ? qscale : nullptr,
-                               fp8 ? ix.cent_scales : nullptr, S);
-  SOAR_LAUNCHED();
+  score_centroids(ix, Qf, qscale, nq, qstride, S, s);
   const int t2 = pow2_at_least(t);
-  const int smem = t2 * 8;
+  const int smem = t2 * 8 + (ix.c <= kToptSmemRow ? ix.c * 4 : 0);
   SOAR_CUDA(cudaFuncSetAttribute(topt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   topt_kernel<<<(unsigned)nq, 256, smem, s>>>(S, ix.c, t, t2, top, top_s);
   SOAR_LAUNCHED();
@@ -734,13 +835,9 @@ void select_partitions_in(const IndexData& ix, const void* Q, soar_dtype dt, int
   float* S = reinterpret_cast<float*>(base);
   // every scratch element read below is first written here: nothing to clear
   prep_any(Q, dt, nq, ix.d, qstride, fp8, Qf, qscale, s);
-  dim3 grid(ceil_div(ix.c, 64), ceil_div(nq, 64));
-  gemm_nt<<<grid, 256, 0, s>>>(Qf, nq, qstride, fp8 ? ix.cent_code_vals : ix.centroids, ix.c,
-                               fp8 ? ix.code_stride : ix.d, ix.d, fp8 ? qscale : nullptr,
-                               fp8 ? ix.cent_scales : nullptr, S);
-  SOAR_LAUNCHED();
+  score_centroids(ix, Qf, qscale, nq, qstride, S, s);
   const int t2 = pow2_at_least(t);
-  const int smem = t2 * 8;
+  const int smem = t2 * 8 + (ix.c <= kToptSmemRow ? ix.c * 4 : 0);
   SOAR_CUDA(cudaFuncSetAttribute(topt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   topt_kernel<<<(unsigned)nq, 256, smem, s>>>(S, ix.c, t, t2, top, top_scores);
   SOAR_LAUNCHED();
