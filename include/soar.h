@@ -232,6 +232,55 @@ SOAR_API soar_status soar_select_partitions_static(const soar_index* index, cons
                                                    int64_t nq, int32_t t, int32_t* top_out, float* score_out,
                                                    cudaStream_t stream);
 
+/* ------------------------------------------------------------------ *
+ * Learned probe count (an extension; the paper has no counterpart)
+ * ------------------------------------------------------------------ *
+ * A small MLP predicts, per query, how many partitions to probe.  Input
+ * z(q) = [q || the query's top-`top` centroid scores, descending]
+ * (d_in = d + top); two hidden layers of `hidden` units with ReLU; one
+ * output y, trained by mean squared error against log t*(q).  Parameters are
+ * one fp32 device buffer of soar_mlp_param_count(d_in, hidden) values laid
+ * out W1 [hidden][d_in] | b1 [hidden] | W2 [hidden][hidden] | b2 [hidden] |
+ * W3 [hidden] | b3 [1] (row-major); the caller initialises it.  With bf16 != 0
+ * every product rounds its operands to bf16 and accumulates in fp32.
+ */
+SOAR_API int64_t soar_mlp_param_count(int32_t d_in, int32_t hidden);
+
+/* Z_out [nq][d + top] fp32 features (top <= min(c, 8192)). */
+SOAR_API soar_status soar_probe_features(const soar_index* index, const void* Q, soar_dtype dtype, int64_t nq,
+                                         int32_t top, float* Z_out, cudaStream_t stream);
+
+/* labels_out [nq] int32: t*(q), the smallest probe count whose recall@k reaches
+ * target_recall, given the query's exact top-k `truth_ids` [nq][k] (int64,
+ * e.g. from soar_exact_mips).  A neighbour is found at probe count t when one
+ * of its partitions has position <= t in the query's probe order (ties to the
+ * lower id); t* is the ceil(target_recall * k)-th smallest such position. */
+SOAR_API soar_status soar_probe_labels(const soar_index* index, const void* Q, soar_dtype dtype, int64_t nq,
+                                       const int64_t* truth_ids, int32_t k, float target_recall,
+                                       int32_t* labels_out, cudaStream_t stream);
+
+/* y_out [batch] = network output for Z [batch][d_in]. */
+SOAR_API soar_status soar_mlp_forward(const float* params, int32_t d_in, int32_t hidden, const float* Z,
+                                      int32_t batch, int32_t bf16, float* y_out, cudaStream_t stream);
+
+/* grads_out (same layout as params) = d/dparams of mean((y - target)^2) over
+ * the batch; loss_out (device float, may be NULL) = that loss. */
+SOAR_API soar_status soar_mlp_backward(const float* params, int32_t d_in, int32_t hidden, const float* Z,
+                                       const float* target, int32_t batch, int32_t bf16, float* grads_out,
+                                       float* loss_out, cudaStream_t stream);
+
+/* One Adam step (bias-corrected, step counted from 1) on `count` parameters;
+ * m1, m2 are the caller's moment buffers (start at zero). */
+SOAR_API soar_status soar_mlp_adam(float* params, const float* grads, float* m1, float* m2, int64_t count,
+                                   int32_t step, float lr, float beta1, float beta2, float eps,
+                                   cudaStream_t stream);
+
+/* t_out [batch] = clamp(ceil(alpha * exp(y)), 1, c): per-query probe counts
+ * for soar_search's t_per_query. */
+SOAR_API soar_status soar_mlp_predict_probes(const float* params, int32_t d_in, int32_t hidden, const float* Z,
+                                             int32_t batch, int32_t bf16, float alpha, int32_t c, int32_t* t_out,
+                                             cudaStream_t stream);
+
 /*
  * Synchronises the current device and reports device-side failures of
  * earlier calls: SOAR_ETIMEOUT when a kernel gave up one of its bounded

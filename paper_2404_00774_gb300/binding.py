@@ -54,6 +54,13 @@ _SIGS = {
     "soar_quantize_fp8": ([_P, _I32, _I64, _I32, _P, _I32, _P, _P], _I32),
     "soar_select_partitions_static": ([_P, _P, _I32, _I64, _I32, _P, _P, _P], _I32),
     "soar_check_device": ([], _I32),
+    "soar_mlp_param_count": ([_I32, _I32], _I64),
+    "soar_probe_features": ([_P, _P, _I32, _I64, _I32, _P, _P], _I32),
+    "soar_probe_labels": ([_P, _P, _I32, _I64, _P, _I32, _F32, _P, _P], _I32),
+    "soar_mlp_forward": ([_P, _I32, _I32, _P, _I32, _I32, _P, _P], _I32),
+    "soar_mlp_backward": ([_P, _I32, _I32, _P, _P, _I32, _I32, _P, _P, _P], _I32),
+    "soar_mlp_adam": ([_P, _P, _P, _P, _I64, _I32, _F32, _F32, _F32, _F32, _P], _I32),
+    "soar_mlp_predict_probes": ([_P, _I32, _I32, _P, _I32, _I32, _F32, _I32, _P, _P], _I32),
     "soar_kernel_launches": ([], ct.c_uint64),
     "soar_stage_timing": ([_I32], _I32),
     "soar_stage_times": ([ct.c_char_p, _I32, _P, _P, _I32], _I32),
@@ -296,3 +303,69 @@ def soar_stage_times() -> dict:
     m = load().soar_stage_times(names, 1024, ct.cast(ms, ct.c_void_p), ct.cast(cnt, ct.c_void_p), 32)
     keys = names.value.decode().split(",") if m else []
     return {keys[i]: (float(ms[i]), int(cnt[i])) for i in range(m)}
+
+
+# ---------------------------------------------------------------- learned probe count
+
+def soar_mlp_param_count(d_in: int, hidden: int) -> int:
+    return int(load().soar_mlp_param_count(d_in, hidden))
+
+
+def soar_probe_features(index: Index, Q: torch.Tensor, top: int = 64, stream=None) -> torch.Tensor:
+    nq, d = Q.shape
+    Z = torch.empty((nq, d + top), dtype=torch.float32, device=Q.device)
+    _check(load().soar_probe_features(index.handle, _dev(Q, "Q", ndim=2), _dtype(Q), nq, top, _dev(Z, "Z"),
+                                      _stream(stream)))
+    return Z
+
+
+def soar_probe_labels(index: Index, Q: torch.Tensor, truth: torch.Tensor, target: float = 0.9,
+                      stream=None) -> torch.Tensor:
+    nq = Q.shape[0]
+    k = truth.shape[1]
+    out = torch.empty((nq,), dtype=torch.int32, device=Q.device)
+    _check(load().soar_probe_labels(index.handle, _dev(Q, "Q", ndim=2), _dtype(Q), nq,
+                                    _dev(truth, "truth", torch.int64, 2), k, float(target), _dev(out, "labels"),
+                                    _stream(stream)))
+    return out
+
+
+def soar_mlp_forward(params: torch.Tensor, d_in: int, hidden: int, Z: torch.Tensor, bf16: bool = False,
+                     stream=None) -> torch.Tensor:
+    B = Z.shape[0]
+    y = torch.empty((B,), dtype=torch.float32, device=Z.device)
+    _check(load().soar_mlp_forward(_dev(params, "params", torch.float32, 1), d_in, hidden,
+                                   _dev(Z, "Z", torch.float32, 2), B, int(bf16), _dev(y, "y"), _stream(stream)))
+    return y
+
+
+def soar_mlp_backward(params: torch.Tensor, d_in: int, hidden: int, Z: torch.Tensor, target: torch.Tensor,
+                      bf16: bool = False, grads: torch.Tensor | None = None, loss: torch.Tensor | None = None,
+                      stream=None):
+    B = Z.shape[0]
+    if grads is None:
+        grads = torch.empty_like(params)
+    if loss is None:
+        loss = torch.empty((1,), dtype=torch.float32, device=Z.device)
+    _check(load().soar_mlp_backward(_dev(params, "params", torch.float32, 1), d_in, hidden,
+                                    _dev(Z, "Z", torch.float32, 2), _dev(target, "target", torch.float32, 1), B,
+                                    int(bf16), _dev(grads, "grads", torch.float32, 1),
+                                    _dev(loss, "loss", torch.float32, 1), _stream(stream)))
+    return grads, loss
+
+
+def soar_mlp_adam(params: torch.Tensor, grads: torch.Tensor, m1: torch.Tensor, m2: torch.Tensor, step: int,
+                  lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, stream=None) -> None:
+    _check(load().soar_mlp_adam(_dev(params, "params", torch.float32, 1), _dev(grads, "grads", torch.float32, 1),
+                                _dev(m1, "m1", torch.float32, 1), _dev(m2, "m2", torch.float32, 1),
+                                params.numel(), step, lr, beta1, beta2, eps, _stream(stream)))
+
+
+def soar_mlp_predict_probes(params: torch.Tensor, d_in: int, hidden: int, Z: torch.Tensor, alpha: float, c: int,
+                            bf16: bool = False, stream=None) -> torch.Tensor:
+    B = Z.shape[0]
+    t = torch.empty((B,), dtype=torch.int32, device=Z.device)
+    _check(load().soar_mlp_predict_probes(_dev(params, "params", torch.float32, 1), d_in, hidden,
+                                          _dev(Z, "Z", torch.float32, 2), B, int(bf16), float(alpha), c,
+                                          _dev(t, "t"), _stream(stream)))
+    return t

@@ -289,6 +289,74 @@ soar_status soar_select_partitions_static(const soar_index* index, const void* Q
   });
 }
 
+int64_t soar_mlp_param_count(int32_t d_in, int32_t hidden) {
+  return d_in > 0 && hidden > 0 ? soar::mlp_param_count(d_in, hidden) : -1;
+}
+
+soar_status soar_probe_features(const soar_index* index, const void* Q, soar_dtype dtype, int64_t nq, int32_t top,
+                                float* Z_out, cudaStream_t stream) {
+  return guarded([&] {
+    SOAR_REQUIRE(index && Q && Z_out, "null pointer");
+    SOAR_REQUIRE(valid_dtype(dtype), "unknown dtype");
+    SOAR_REQUIRE(nq >= 1 && top >= 1 && top <= index->data.c && top <= 8192, "bad sizes");
+    soar::Scratch scr(stream);
+    soar::probe_features(index->data, Q, dtype, nq, top, Z_out, stream, scr);
+  });
+}
+
+soar_status soar_probe_labels(const soar_index* index, const void* Q, soar_dtype dtype, int64_t nq,
+                              const int64_t* truth_ids, int32_t k, float target_recall, int32_t* labels_out,
+                              cudaStream_t stream) {
+  return guarded([&] {
+    SOAR_REQUIRE(index && Q && truth_ids && labels_out, "null pointer");
+    SOAR_REQUIRE(valid_dtype(dtype), "unknown dtype");
+    SOAR_REQUIRE(nq >= 1 && k >= 1 && k <= 1024, "bad sizes");
+    SOAR_REQUIRE(target_recall > 0.f && target_recall <= 1.f, "target_recall must be in (0, 1]");
+    soar::Scratch scr(stream);
+    soar::probe_labels(index->data, Q, dtype, nq, truth_ids, k, target_recall, labels_out, stream, scr);
+  });
+}
+
+soar_status soar_mlp_forward(const float* params, int32_t d_in, int32_t hidden, const float* Z, int32_t batch,
+                             int32_t bf16, float* y_out, cudaStream_t stream) {
+  return guarded([&] {
+    SOAR_REQUIRE(params && Z && y_out, "null pointer");
+    SOAR_REQUIRE(d_in >= 1 && hidden >= 1 && batch >= 1, "bad sizes");
+    soar::Scratch scr(stream);
+    soar::mlp_predict(params, d_in, hidden, Z, batch, bf16 != 0, 1.f, 1, y_out, nullptr, stream, scr);
+  });
+}
+
+soar_status soar_mlp_backward(const float* params, int32_t d_in, int32_t hidden, const float* Z, const float* target,
+                              int32_t batch, int32_t bf16, float* grads_out, float* loss_out, cudaStream_t stream) {
+  return guarded([&] {
+    SOAR_REQUIRE(params && Z && target && grads_out, "null pointer");
+    SOAR_REQUIRE(d_in >= 1 && hidden >= 1 && batch >= 1, "bad sizes");
+    soar::Scratch scr(stream);
+    soar::mlp_backward(params, d_in, hidden, Z, target, batch, bf16 != 0, grads_out, loss_out, stream, scr);
+  });
+}
+
+soar_status soar_mlp_adam(float* params, const float* grads, float* m1, float* m2, int64_t count, int32_t step,
+                          float lr, float beta1, float beta2, float eps, cudaStream_t stream) {
+  return guarded([&] {
+    SOAR_REQUIRE(params && grads && m1 && m2, "null pointer");
+    SOAR_REQUIRE(count >= 1 && step >= 1 && std::isfinite(lr), "bad arguments");
+    soar::mlp_adam(params, grads, m1, m2, count, step, lr, beta1, beta2, eps, stream);
+  });
+}
+
+soar_status soar_mlp_predict_probes(const float* params, int32_t d_in, int32_t hidden, const float* Z, int32_t batch,
+                                    int32_t bf16, float alpha, int32_t c, int32_t* t_out, cudaStream_t stream) {
+  return guarded([&] {
+    SOAR_REQUIRE(params && Z && t_out, "null pointer");
+    SOAR_REQUIRE(d_in >= 1 && hidden >= 1 && batch >= 1 && c >= 1, "bad sizes");
+    SOAR_REQUIRE(std::isfinite(alpha) && alpha > 0.f, "alpha must be finite and > 0");
+    soar::Scratch scr(stream);
+    soar::mlp_predict(params, d_in, hidden, Z, batch, bf16 != 0, alpha, c, nullptr, t_out, stream, scr);
+  });
+}
+
 soar_status soar_check_device(void) {
   return guarded([&] {
     SOAR_CUDA(cudaDeviceSynchronize());

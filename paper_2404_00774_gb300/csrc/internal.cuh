@@ -63,6 +63,7 @@ struct IndexData {
   float* tc_pmax = nullptr;       // [c] largest ||x|| of each partition
   int32_t tc_kp = 0;
   int64_t tc_groups = 0;
+  int32_t* assign = nullptr;      // [n][1 + spills] copy of the assignment
 };
 
 void build_index(IndexData& ix, const void* X, soar_dtype dt, const float* C, const int32_t* assign,
@@ -76,6 +77,24 @@ void quantize_fp8(const void* V, soar_dtype dt, int64_t m, int32_t d, uint8_t* c
 
 void select_partitions(const IndexData& ix, const void* Q, soar_dtype dt, int64_t nq, int32_t t,
                        int32_t* top, float* top_scores, cudaStream_t s, Scratch& scr);
+// S [nq][c] = the centroid scores the search ranks partitions by.
+void centroid_scores(const IndexData& ix, const void* Q, soar_dtype dt, int64_t nq, float* S, cudaStream_t s,
+                     Scratch& scr);
+
+// ----------------------------------------------------------- mlp.cu
+int64_t mlp_param_count(int D, int H);
+void mlp_forward(const float* P, int D, int H, const float* Z, int B, bool bf16, float* A1, float* H1, float* A2,
+                 float* H2, float* y, cudaStream_t s);
+void mlp_backward(const float* P, int D, int H, const float* Z, const float* target, int B, bool bf16, float* G,
+                  float* loss, cudaStream_t s, Scratch& scr);
+void mlp_adam(float* P, const float* G, float* m1, float* m2, int64_t n, int step, float lr, float b1, float b2,
+              float eps, cudaStream_t s);
+void mlp_predict(const float* P, int D, int H, const float* Z, int B, bool bf16, float alpha, int c, float* y_out,
+                 int32_t* t_out, cudaStream_t s, Scratch& scr);
+void probe_features(const IndexData& ix, const void* Q, soar_dtype dt, int64_t nq, int top, float* Z,
+                    cudaStream_t s, Scratch& scr);
+void probe_labels(const IndexData& ix, const void* Q, soar_dtype dt, int64_t nq, const int64_t* truth, int k,
+                  float target, int32_t* labels, cudaStream_t s, Scratch& scr);
 
 // Same computation as select_partitions with all scratch carved from a
 // caller-provided device buffer of select_scratch_bytes(ix, nq) bytes.

@@ -172,6 +172,8 @@ void build_index(IndexData& ix, const void* X, soar_dtype dt, const float* C, co
   dev_alloc((void**)&ix.ids, sizeof(int32_t) * rows);
   dev_alloc((void**)&ix.centroids, sizeof(float) * (size_t)c * d);
   SOAR_CUDA(cudaMemcpyAsync(ix.centroids, C, sizeof(float) * (size_t)c * d, cudaMemcpyDeviceToDevice, s));
+  dev_alloc((void**)&ix.assign, sizeof(int32_t) * (size_t)n * a);
+  SOAR_CUDA(cudaMemcpyAsync(ix.assign, assign, sizeof(int32_t) * (size_t)n * a, cudaMemcpyDeviceToDevice, s));
 
   uint32_t* keys = scr.get<uint32_t>(rows);
   int32_t* vals = scr.get<int32_t>(rows);
@@ -282,7 +284,7 @@ void build_index(IndexData& ix, const void* X, soar_dtype dt, const float* C, co
 void free_index(IndexData& ix) {
   void* ptrs[] = {ix.offsets, ix.ids, ix.vectors, ix.row_scales, ix.originals, ix.centroids,
                   ix.part_order, ix.cent_code_vals, ix.cent_scales, ix.tc_rows, ix.tc_gstart,
-                  ix.tc_ids, ix.tc_norms, ix.tc_pmax};
+                  ix.tc_ids, ix.tc_norms, ix.tc_pmax, ix.assign};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   ix = IndexData{};

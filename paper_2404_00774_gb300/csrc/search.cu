@@ -804,6 +804,16 @@ __global__ void query_norms(const float* __restrict__ Qf, int64_t nq, int stride
 
 }  // namespace
 
+void centroid_scores(const IndexData& ix, const void* Q, soar_dtype dt, int64_t nq, float* S, cudaStream_t s,
+                     Scratch& scr) {
+  const bool fp8 = ix.mode == SOAR_SCORE_FP8;
+  const int qstride = fp8 ? ix.code_stride : (ix.d + 3) / 4 * 4;
+  float* Qf = scr.get<float>((size_t)nq * qstride);
+  float* qscale = fp8 ? scr.get<float>(nq) : nullptr;
+  prep_any(Q, dt, nq, ix.d, qstride, fp8, Qf, qscale, s);
+  score_centroids(ix, Qf, qscale, nq, qstride, S, s);
+}
+
 void select_partitions(const IndexData& ix, const void* Q, soar_dtype dt, int64_t nq, int32_t t, int32_t* top,
                        float* top_scores, cudaStream_t s, Scratch& scr) {
   const bool fp8 = ix.mode == SOAR_SCORE_FP8;
