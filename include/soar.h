@@ -281,6 +281,52 @@ SOAR_API soar_status soar_mlp_predict_probes(const float* params, int32_t d_in, 
                                              int32_t batch, int32_t bf16, float alpha, int32_t c, int32_t* t_out,
                                              cudaStream_t stream);
 
+/* ------------------------------------------------------------------ *
+ * Serving loop (an extension; the paper describes no serving system)
+ * ------------------------------------------------------------------ *
+ * Continuous batching over a resident SOAR_SCORE_F32 index.  Requests (one
+ * fp32 host query of d values, its own k and t) are queued from any thread;
+ * a dispatcher thread keeps up to `streams` batches in flight, each on its own
+ * CUDA stream.  Whenever a stream slot is free it forms the next batch from
+ * the pending requests in arrival order, admitting requests while the batch
+ * holds at most max_batch queries and the estimated device scratch of all
+ * batches in flight stays within memory_budget bytes (a request alone is
+ * always admitted when nothing runs).  A batch is one soar_search with
+ * per-request probe counts and the batch's largest k; each request receives
+ * its own top k.  The index must outlive the server.
+ */
+typedef struct {
+  int32_t max_batch;       /* queries per batch, 1..4096 */
+  int32_t streams;         /* batches in flight, 1..16 */
+  int64_t memory_budget;   /* bytes of device scratch admitted in flight */
+  int32_t max_k;           /* largest k a request may ask for, 1..1024 */
+} soar_server_config;
+
+typedef struct {
+  uint64_t batches;            /* batches launched */
+  uint64_t completed;          /* requests completed */
+  uint64_t queries_in_batches; /* requests launched (sum of batch sizes) */
+  uint64_t pending;            /* requests waiting for a batch */
+  int32_t max_in_flight;       /* most batches seen on the GPU at once */
+  double p50_ms, p99_ms;       /* request latency (submit to results on the host) */
+} soar_server_metrics;
+
+typedef struct soar_server soar_server;
+
+SOAR_API soar_status soar_server_create(const soar_index* index, const soar_server_config* cfg,
+                                        soar_server** out /* host */);
+/* query: host [d] fp32 (copied); request_id: host out.  1 <= k <= max_k, 1 <= t <= min(c, 8192). */
+SOAR_API soar_status soar_server_submit(soar_server* server, const float* query, int32_t k, int32_t t,
+                                        uint64_t* request_id);
+/* Blocks until the request completed (or timeout_ms passed: SOAR_ETIMEOUT) and
+ * copies its k ids / scores to host memory; latency_ms (may be NULL) receives
+ * submit-to-completion time.  Each request can be collected once. */
+SOAR_API soar_status soar_server_wait(soar_server* server, uint64_t request_id, int64_t* ids_out, float* scores_out,
+                                      double* latency_ms, int32_t timeout_ms);
+SOAR_API soar_status soar_server_stats(soar_server* server, soar_server_metrics* out /* host */);
+/* Finishes the queued requests, stops the dispatcher and frees the server. */
+SOAR_API soar_status soar_server_destroy(soar_server* server);
+
 /*
  * Synchronises the current device and reports device-side failures of
  * earlier calls: SOAR_ETIMEOUT when a kernel gave up one of its bounded

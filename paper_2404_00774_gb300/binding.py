@@ -11,6 +11,7 @@ from __future__ import annotations
 import ctypes as ct
 import os
 
+import numpy as np
 import torch
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -29,6 +30,17 @@ class SoarError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
         self.status = status
+
+
+class ServerConfig(ct.Structure):
+    _fields_ = [("max_batch", ct.c_int32), ("streams", ct.c_int32), ("memory_budget", ct.c_int64),
+                ("max_k", ct.c_int32)]
+
+
+class ServerStats(ct.Structure):
+    _fields_ = [("batches", ct.c_uint64), ("completed", ct.c_uint64), ("queries_in_batches", ct.c_uint64),
+                ("pending", ct.c_uint64), ("max_in_flight", ct.c_int32), ("p50_ms", ct.c_double),
+                ("p99_ms", ct.c_double)]
 
 
 class IndexInfo(ct.Structure):
@@ -54,6 +66,11 @@ _SIGS = {
     "soar_quantize_fp8": ([_P, _I32, _I64, _I32, _P, _I32, _P, _P], _I32),
     "soar_select_partitions_static": ([_P, _P, _I32, _I64, _I32, _P, _P, _P], _I32),
     "soar_check_device": ([], _I32),
+    "soar_server_create": ([_P, ct.POINTER(ServerConfig), ct.POINTER(_P)], _I32),
+    "soar_server_submit": ([_P, _P, _I32, _I32, ct.POINTER(ct.c_uint64)], _I32),
+    "soar_server_wait": ([_P, ct.c_uint64, _P, _P, ct.POINTER(ct.c_double), _I32], _I32),
+    "soar_server_stats": ([_P, ct.POINTER(ServerStats)], _I32),
+    "soar_server_destroy": ([_P], _I32),
     "soar_mlp_param_count": ([_I32, _I32], _I64),
     "soar_probe_features": ([_P, _P, _I32, _I64, _I32, _P, _P], _I32),
     "soar_probe_labels": ([_P, _P, _I32, _I64, _P, _I32, _F32, _P, _P], _I32),
@@ -369,3 +386,57 @@ def soar_mlp_predict_probes(params: torch.Tensor, d_in: int, hidden: int, Z: tor
                                           _dev(Z, "Z", torch.float32, 2), B, int(bf16), float(alpha), c,
                                           _dev(t, "t"), _stream(stream)))
     return t
+
+
+# ---------------------------------------------------------------- serving loop
+
+class Server:
+    """Continuous-batching server over an index (soar_server_* of the C ABI)."""
+
+    def __init__(self, index: Index, max_batch: int = 256, streams: int = 2, memory_budget: int = 1 << 30,
+                 max_k: int = 100):
+        self.index = index                      # keeps the index alive
+        self.max_k = max_k
+        self.d = index.info.d
+        cfg = ServerConfig(max_batch, streams, memory_budget, max_k)
+        h = ct.c_void_p()
+        st = load().soar_server_create(index.handle, ct.byref(cfg), ct.byref(h))
+        if st != SOAR_OK:
+            raise SoarError(st, "soar_server_create failed")
+        self._h = h
+
+    def submit(self, q: np.ndarray, k: int, t: int) -> int:
+        q = np.ascontiguousarray(q, dtype=np.float32)
+        if q.shape != (self.d,):
+            raise ValueError(f"query must have shape ({self.d},)")
+        rid = ct.c_uint64()
+        st = load().soar_server_submit(self._h, q.ctypes.data_as(ct.c_void_p), k, t, ct.byref(rid))
+        if st != SOAR_OK:
+            raise SoarError(st, "soar_server_submit rejected the request")
+        return int(rid.value)
+
+    def wait(self, rid: int, k: int, timeout_ms: int = 60000):
+        ids = np.empty(k, dtype=np.int64)
+        sc = np.empty(k, dtype=np.float32)
+        lat = ct.c_double()
+        st = load().soar_server_wait(self._h, rid, ids.ctypes.data_as(ct.c_void_p), sc.ctypes.data_as(ct.c_void_p),
+                                     ct.byref(lat), timeout_ms)
+        if st != SOAR_OK:
+            raise SoarError(st, f"request {rid} failed")
+        return ids, sc, float(lat.value)
+
+    def stats(self) -> dict:
+        out = ServerStats()
+        _check(load().soar_server_stats(self._h, ct.byref(out)))
+        return {name: getattr(out, name) for name, _ in ServerStats._fields_}
+
+    def close(self):
+        if self._h is not None:
+            load().soar_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

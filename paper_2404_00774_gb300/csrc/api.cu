@@ -7,10 +7,6 @@
 
 #include "internal.cuh"
 
-struct soar_index {
-  soar::IndexData data;
-};
-
 namespace soar {
 
 std::atomic<uint64_t> g_launches{0};

@@ -66,6 +66,15 @@ struct IndexData {
   int32_t* assign = nullptr;      // [n][1 + spills] copy of the assignment
 };
 
+}  // namespace soar
+
+// The opaque handle of the C ABI.
+struct soar_index {
+  soar::IndexData data;
+};
+
+namespace soar {
+
 void build_index(IndexData& ix, const void* X, soar_dtype dt, const float* C, const int32_t* assign,
                  cudaStream_t s);
 void free_index(IndexData& ix);
