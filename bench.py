@@ -60,6 +60,7 @@ def parse_args():
     p.add_argument("--nq", type=int, default=None, help="queries per step per GPU")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=300, help="queries timed on the CPU oracle")
+    p.add_argument("--no-extras", action="store_true", help="skip the learned-probe and serving measurements")
     return p.parse_args()
 
 
@@ -161,7 +162,7 @@ def find_t(sb, index, Qd, truth, k, t_max):
 
 def kernel_hash():
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_2404_00774_gb300", "csrc", "search.cu"), "rb") as f:
+    with open(os.path.join(ROOT, "paper_2404_00774_gb300", "csrc", "scan_tc.cu"), "rb") as f:
         h.update(f.read())
     return h.hexdigest()[:16]
 
@@ -169,7 +170,7 @@ def kernel_hash():
 def profiled_traffic(workload):
     """Per-launch DRAM bytes of the scan kernel from a committed ncu summary,
     if that summary was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", f"scan_kernel_{workload}.txt")
+    path = os.path.join(ROOT, "profiles", f"scan_tc_kernel_{workload}.txt")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
@@ -243,6 +244,88 @@ def run_reference(args):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+# ------------------------------------------------------------------ extensions
+
+def learned_probe_arm(sb, ix, mix, w, Xd, Qd, truth, k, soar_arm, step_times, n_train=100_000, steps=1500):
+    """Train the probe-count MLP on fresh mixture queries (GPU labels), pick
+    alpha for recall >= target on a calibration set, then time the search of
+    the benchmark queries with per-query probe counts."""
+    import torch
+    from paper_2404_00774_gb300 import probe
+    t0 = time.perf_counter()
+    Qtr = torch.from_numpy(mix.sample(n_train, 304)).to(Qd.device)
+    Qcal = torch.from_numpy(mix.sample(4000, 305)).to(Qd.device)
+    truth_tr = torch.cat([sb.soar_exact_mips(Xd, Qtr[i:i + 10000], k)[0] for i in range(0, n_train, 10000)])
+    truth_cal = sb.soar_exact_mips(Xd, Qcal, k)[0]
+    Ztr = sb.soar_probe_features(ix, Qtr, 64)
+    labels = sb.soar_probe_labels(ix, Qtr, truth_tr, RECALL_TARGET)
+    params, losses = probe.train(ix, Ztr, labels, hidden=256, steps=steps, batch=4096, lr=1e-3, bf16=True)
+    Zcal = sb.soar_probe_features(ix, Qcal, 64)
+    alpha = probe.calibrate_alpha(ix, params, 256, Zcal, Qcal, truth_cal, k, w.c)
+    train_s = time.perf_counter() - t0
+    # timed: features + MLP + search, per step, the whole query batch
+    import statistics as st
+
+    def step():
+        Z = sb.soar_probe_features(ix, Qd, 64)
+        t = sb.soar_mlp_predict_probes(params, Z.shape[1], 256, Z, alpha, w.c, True)
+        return sb.soar_search(ix, Qd, k, int(t.max()), t_per_query=t), t
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    ts = []
+    stream = torch.cuda.current_stream()
+    for i in range(10):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        (ids, _), t = step()
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    rec = float((ids[:, :, None] == truth[:, None, :]).any(dim=2).float().mean())
+    ms = st.mean(ts)
+    return {"recall": rec, "mean_t": float(t.float().mean()), "max_t": int(t.max()), "alpha": alpha,
+            "qps": Qd.shape[0] / (ms / 1e3), "ms_per_step": ms, "fixed_t": soar_arm["t"],
+            "fixed_t_qps": soar_arm.get("qps"), "train_queries": n_train, "train_steps": steps,
+            "final_train_loss": losses[-1], "setup_s": train_s}
+
+
+def serving_arm(sb, ix, Q, k, rates=(200_000, 1_000_000, 4_000_000), n_req=20000):
+    """Poisson arrivals of single-query requests (k in {10, 100}, t in
+    [8, 64]) into the continuous-batching server; p50 / p99 latency and the
+    completed throughput per offered rate."""
+    import threading
+    out = []
+    kk, tt = synth.request_mix(n_req, seed=505, ks=(10, 100), t_lo=8, t_hi=64)
+    for rate in rates:
+        arrivals = synth.poisson_arrivals(rate, n_req, seed=504)
+        srv = sb.Server(ix, max_batch=1024, streams=3, memory_budget=4 << 30, max_k=100)
+        rids = [0] * n_req
+        t0 = time.perf_counter()
+
+        def produce():
+            for i in range(n_req):
+                delay = arrivals[i] - (time.perf_counter() - t0)
+                if delay > 0:
+                    time.sleep(delay)
+                rids[i] = srv.submit(Q[i % Q.shape[0]], int(kk[i]), int(tt[i]))
+
+        th = threading.Thread(target=produce)
+        th.start()
+        th.join()
+        for i in range(n_req):
+            srv.wait(rids[i], int(kk[i]))
+        wall = time.perf_counter() - t0
+        stats = srv.stats()
+        srv.close()
+        out.append({"offered_qps": rate, "achieved_qps": n_req / wall, "p50_ms": stats["p50_ms"],
+                    "p99_ms": stats["p99_ms"], "batches": stats["batches"],
+                    "mean_batch": stats["queries_in_batches"] / max(1, stats["batches"]),
+                    "max_in_flight": stats["max_in_flight"]})
+    return {"requests_per_rate": n_req, "k": [10, 100], "t_range": [8, 64], "rates": out}
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -348,7 +431,9 @@ def run_ours(args):
         ts = []
         for i in range(args.steps):
             flush.fill_(float(i))
+            torch.cuda.nvtx.range_push("timed")       # lets ncu capture exactly the timed steps
             (_, ms) = timed(lambda: sb.soar_search(ix, Qd, k, t_main))
+            torch.cuda.nvtx.range_pop()
             ts.append(ms)
         sb.soar_stage_timing(False)
         torch.cuda.synchronize()
@@ -393,24 +478,39 @@ def run_ours(args):
     dsq, top = datapoints_searched(sb, ix, Qd, t_main, offsets)
     pairs_rows = float(dsq.sum())                      # (query, row) pairs scored per launch
     flops = 2.0 * w.d * pairs_rows
-    probed = torch.unique(top)
+    # rows streamed: each partition once per chunk of <= 128 of its queries
+    m_p = torch.bincount(top.reshape(-1), minlength=w.c)
     sizes = (offsets[1:] - offsets[:-1])
-    rows_read = float(sizes[probed].sum())
-    row_bytes = ix.info.row_stride * 4 + 4
-    bytes_alg = rows_read * row_bytes + nq * ix.info.row_stride * 4 + nq * t_main * k * 8
-    alu_peak = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12     # TFLOP/s
+    chunks = (m_p + 127) // 128
+    rows_read = float((chunks * sizes).sum())
+    kp = (w.d + 7) // 8 * 8
+    bytes_alg = rows_read * kp * 4 + nq * kp * 4 + nq * t_main * (32 * 8 + 8)
+    tf32_peak = bf16 * 0.5                              # nominal tf32:bf16 dense rate is 1:2
     tflops = flops / (scan_ms_per / 1e3) / 1e12
     gbs = bytes_alg / (scan_ms_per / 1e3) / 1e9
-    if tflops / alu_peak >= gbs / hbm:
-        roof = {"bound": "alu", "achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": tflops / alu_peak, "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
+    if tflops / tf32_peak >= gbs / hbm:
+        roof = {"bound": "tensor", "achieved": tflops, "peak": tf32_peak, "unit": "TFLOP/s",
+                "frac": tflops / tf32_peak, "peak_source": f"{peak_src} bf16_tflops x 0.5 (tf32)"}
     else:
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
                 "peak_source": f"{peak_src} hbm_gbs"}
     traffic = profiled_traffic(args.workload)
-    roof.update({"traffic": traffic, "kernel": "scan_kernel", "ms_per_launch": scan_ms_per,
+    roof.update({"traffic": traffic, "kernel": "scan_tc_kernel", "ms_per_launch": scan_ms_per,
                  "algorithmic_bytes": bytes_alg, "algorithmic_flops": flops,
-                 "hbm_gbs_achieved": gbs, "hbm_frac": gbs / hbm, "alu_tflops_achieved": tflops})
+                 "hbm_gbs_achieved": gbs, "hbm_frac": gbs / hbm, "tf32_tflops_achieved": tflops})
+
+    # ---- learned probe count (extension): trained on GPU labels, same recall target
+    extras = {}
+    if not args.no_extras:
+        try:
+            extras["learned_probe"] = learned_probe_arm(sb, ix, mix, w, Xd, Qd, truth, k, results["soar"],
+                                                        step_times)
+        except Exception as e:  # reported, never fatal for the metric
+            extras["learned_probe"] = {"error": str(e)[:200]}
+        try:
+            extras["serving"] = serving_arm(sb, ix, Q, k)
+        except Exception as e:
+            extras["serving"] = {"error": str(e)[:200]}
 
     # ---- CPU oracle baseline (rank 0 only, N = 1 only)
     cpu = None
@@ -442,6 +542,7 @@ def run_ours(args):
         "build": {"kmeans_ms": km_ms, "assign_ms": assign_ms["soar"],
                   "assignments_per_s": w.n / (assign_ms["soar"] / 1e3), "ground_truth_ms": gt_ms},
         "stages_ms_per_step": {s: v[0] / max(1, v[1]) for s, v in stages.items()},
+        **extras,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
