@@ -291,9 +291,10 @@ SOAR_API soar_status soar_mlp_predict_probes(const float* params, int32_t d_in, 
  * the pending requests in arrival order, admitting requests while the batch
  * holds at most max_batch queries and the estimated device scratch of all
  * batches in flight stays within memory_budget bytes (a request alone is
- * always admitted when nothing runs).  A batch is one soar_search with
- * per-request probe counts and the batch's largest k; each request receives
- * its own top k.  The index must outlive the server.
+ * always admitted when nothing runs) and holds requests of one k class
+ * (k <= 32 or k > 32; the other class keeps its place in the queue).  A batch
+ * is one soar_search with per-request probe counts and the batch's largest k;
+ * each request receives its own top k.  The index must outlive the server.
  */
 typedef struct {
   int32_t max_batch;       /* queries per batch, 1..4096 */
@@ -318,6 +319,23 @@ SOAR_API soar_status soar_server_create(const soar_index* index, const soar_serv
 /* query: host [d] fp32 (copied); request_id: host out.  1 <= k <= max_k, 1 <= t <= min(c, 8192). */
 SOAR_API soar_status soar_server_submit(soar_server* server, const float* query, int32_t k, int32_t t,
                                         uint64_t* request_id);
+/* Queues n requests at once: queries host [n][d] fp32 (copied), ks / ts host
+ * [n] (limits as for soar_server_submit), request_ids host out [n].
+ * arrival_s (host [n], may be NULL): each request's arrival time in seconds
+ * after this call (0 <= arrival_s < 1e6); a request joins the pending queue
+ * when its time comes and its latency counts from then (an open-loop replay
+ * of an arrival trace).  NULL: all arrive now.  Any invalid entry rejects the
+ * whole call (SOAR_EINVAL) before anything is queued. */
+SOAR_API soar_status soar_server_submit_many(soar_server* server, const float* queries, int64_t n, const int32_t* ks,
+                                             const int32_t* ts, const double* arrival_s, uint64_t* request_ids);
+/* Collects n requests in order (each once): ids_out / scores_out host
+ * [n][kstride] receive each request's own k results, the rest of the row
+ * padded with -1 / -inf; latency_ms host [n] may be NULL.  timeout_ms bounds
+ * the whole call (SOAR_ETIMEOUT).  Returns the last failing request status,
+ * else SOAR_OK. */
+SOAR_API soar_status soar_server_wait_many(soar_server* server, const uint64_t* request_ids, int64_t n,
+                                           int32_t kstride, int64_t* ids_out, float* scores_out, double* latency_ms,
+                                           int32_t timeout_ms);
 /* Blocks until the request completed (or timeout_ms passed: SOAR_ETIMEOUT) and
  * copies its k ids / scores to host memory; latency_ms (may be NULL) receives
  * submit-to-completion time.  Each request can be collected once. */

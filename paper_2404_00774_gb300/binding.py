@@ -69,6 +69,8 @@ _SIGS = {
     "soar_server_create": ([_P, ct.POINTER(ServerConfig), ct.POINTER(_P)], _I32),
     "soar_server_submit": ([_P, _P, _I32, _I32, ct.POINTER(ct.c_uint64)], _I32),
     "soar_server_wait": ([_P, ct.c_uint64, _P, _P, ct.POINTER(ct.c_double), _I32], _I32),
+    "soar_server_submit_many": ([_P, _P, _I64, _P, _P, _P, _P], _I32),
+    "soar_server_wait_many": ([_P, _P, _I64, _I32, _P, _P, _P, _I32], _I32),
     "soar_server_stats": ([_P, ct.POINTER(ServerStats)], _I32),
     "soar_server_destroy": ([_P], _I32),
     "soar_mlp_param_count": ([_I32, _I32], _I64),
@@ -414,6 +416,41 @@ class Server:
         if st != SOAR_OK:
             raise SoarError(st, "soar_server_submit rejected the request")
         return int(rid.value)
+
+    def submit_many(self, Q: np.ndarray, ks, ts, arrival_s=None) -> np.ndarray:
+        """Queues len(Q) requests; arrival_s (seconds after the call, or None
+        for now) replays an arrival trace.  Returns the request ids."""
+        Q = np.ascontiguousarray(Q, dtype=np.float32)
+        n = Q.shape[0]
+        if Q.ndim != 2 or Q.shape[1] != self.d:
+            raise ValueError(f"queries must have shape (n, {self.d})")
+        ks = np.ascontiguousarray(np.broadcast_to(ks, (n,)), dtype=np.int32)
+        ts = np.ascontiguousarray(np.broadcast_to(ts, (n,)), dtype=np.int32)
+        arr = None if arrival_s is None else np.ascontiguousarray(arrival_s, dtype=np.float64)
+        if arr is not None and arr.shape != (n,):
+            raise ValueError("arrival_s must have one entry per query")
+        rids = np.empty(n, dtype=np.uint64)
+        st = load().soar_server_submit_many(self._h, Q.ctypes.data_as(ct.c_void_p), n,
+                                            ks.ctypes.data_as(ct.c_void_p), ts.ctypes.data_as(ct.c_void_p),
+                                            None if arr is None else arr.ctypes.data_as(ct.c_void_p),
+                                            rids.ctypes.data_as(ct.c_void_p))
+        if st != SOAR_OK:
+            raise SoarError(st, "soar_server_submit_many rejected the requests")
+        return rids
+
+    def wait_many(self, rids: np.ndarray, kstride: int, timeout_ms: int = 600000):
+        """(ids [n][kstride], scores [n][kstride], latency_ms [n]) of the requests, in order."""
+        rids = np.ascontiguousarray(rids, dtype=np.uint64)
+        n = rids.shape[0]
+        ids = np.empty((n, kstride), dtype=np.int64)
+        sc = np.empty((n, kstride), dtype=np.float32)
+        lat = np.empty(n, dtype=np.float64)
+        st = load().soar_server_wait_many(self._h, rids.ctypes.data_as(ct.c_void_p), n, kstride,
+                                          ids.ctypes.data_as(ct.c_void_p), sc.ctypes.data_as(ct.c_void_p),
+                                          lat.ctypes.data_as(ct.c_void_p), timeout_ms)
+        if st != SOAR_OK:
+            raise SoarError(st, "soar_server_wait_many failed")
+        return ids, sc, lat
 
     def wait(self, rid: int, k: int, timeout_ms: int = 60000):
         ids = np.empty(k, dtype=np.int64)

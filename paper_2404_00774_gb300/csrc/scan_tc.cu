@@ -40,7 +40,21 @@ constexpr int kM = 128;        // query slots per item (MMA M)
 constexpr int kN = 64;         // rows per tile (MMA N)
 constexpr int kThreads = 192;  // 6 warps
 constexpr int kMaxStages = 4;
-constexpr int kCand = 32;      // candidate rows kept per (query, partition)
+constexpr int kCand = 32;      // candidate rows kept per (query, partition), register mode
+constexpr int kWideK = 128;    // largest k of the heap mode
+constexpr int kWideList = 256; // largest global candidate list of the heap mode
+
+// Candidate-list length per (query, partition) slot: kCand for k <= 32, else
+// 2k rounded up to a warp multiple (room to append between compactions).
+__host__ __device__ constexpr int list_len_for(int k) {
+  return k <= kCand ? kCand : ((2 * k + 31) / 32 * 32 > kWideList ? kWideList : (2 * k + 31) / 32 * 32);
+}
+
+// Shared memory behind the tile scores: register mode keeps kCand candidates
+// (score, padded row) per query slot, heap mode a min-heap of k scores.
+__host__ __device__ constexpr size_t ext_bytes(int k) {
+  return k <= kCand ? (size_t)kM * kCand * 8 : (size_t)kM * k * 4;
+}
 
 struct TcParams {
   IvfWork work;
@@ -50,12 +64,13 @@ struct TcParams {
   const float* Qf;         // [nq][kp] fp32 query rows
   const float* qnorm;      // [nq]
   int kp;                  // K, a multiple of 8
-  int k;                   // list length
+  int k;                   // top-k length
+  int kc;                  // candidate-list capacity per pair slot
   int stages;
   int* counter;            // work-item counter
   int* err;                // set to 1 when a wait expired
   unsigned* gbound;        // [nq] per-query lower bound of the final k-th best exact score (ordered key)
-  Cand* cand;              // [pairs][kCand] (ub, padded row) candidates
+  Cand* cand;              // [pairs][kc] (ub, padded row) candidates
   int2* hdr;               // [pairs] (L_k as float bits, count | overflow << 31)
 };
 
@@ -82,9 +97,8 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
   float* av_s = reinterpret_cast<float*>(base + a_bytes + (size_t)S * b_bytes);  // [kN][kM] tile scores
   // per-slot arrays are interleaved slot-fastest ([entry][kM]) so that the 32
   // lanes of a warp always touch 32 distinct banks
-  float* cub_s = av_s + kN * kM;                      // [kCand][kM] candidate scores
-  int32_t* cpos_s = reinterpret_cast<int32_t*>(cub_s + kM * kCand);  // [kCand][kM] padded rows
-  uint64_t* bars = reinterpret_cast<uint64_t*>(cpos_s + kM * kCand);
+  float* ext_s = av_s + kN * kM;   // candidates [kCand][kM] (+ rows) or the heap [k][kM]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(ext_s) + ext_bytes(k));
   // bars: full[S], empty[S], tfull[2], tempty[2]
   __shared__ uint32_t tmem_base_s;
   __shared__ int item_s;
@@ -191,11 +205,19 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
     } else {
       // ---- epilogue: screening bounds and candidate rows per query
       const bool active = jq < nqi;
-      float ta[KMAX];                 // k best screened scores, descending (-inf until filled)
+      // register mode (KMAX > 0): the k best screened scores in registers and
+      // up to kCand candidates in shared memory.  Heap mode (KMAX == 0): the
+      // k best screened scores in a shared-memory min-heap and up to kc
+      // candidates in the slot's global list.
+      float ta[KMAX > 0 ? KMAX : 1];
 #pragma unroll
-      for (int j = 0; j < KMAX; ++j) ta[j] = -INFINITY;
-      float* cub = cub_s + m;
-      int32_t* cpos = cpos_s + m;
+      for (int j = 0; j < (KMAX > 0 ? KMAX : 1); ++j) ta[j] = -INFINITY;
+      float* cub = ext_s + m;                       // register mode: [kCand][kM] scores
+      int32_t* cpos = reinterpret_cast<int32_t*>(ext_s + kM * kCand) + m;   // [kCand][kM] padded rows
+      float* heap = ext_s + m;                      // heap mode: [k][kM]
+      int hn = 0;                                   // heap fill
+      const int64_t eslot = e0 + (active ? jq : 0);
+      Cand* glist = P.cand + eslot * (int64_t)P.kc;  // heap mode: candidates in global memory
       int cnt = 0;
       bool ovf = false;
       const float dlt = ldexpf(qn, -8) * P.pmax[p];   // |s~ - exact| < dlt / 2 for every row of p
@@ -222,7 +244,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
         if (!ok) break;
         const int nvalid = min(kN, nrows - kN * i);
         const int32_t pr0 = (int32_t)((g0 + 8 * i) * 8);
-        if (ak == -INFINITY && k <= 16 && nvalid == kN) {
+        if (KMAX > 0 && ak == -INFINITY && k <= 16 && nvalid == kN) {
           // the k-th largest of 16 group maxima (groups of 4 rows) is a lower
           // bound of the tile's k-th best screened score: seed the cut with it
           float g[16];
@@ -267,23 +289,54 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
           mask |= (uint64_t)(c < nvalid && a >= cut) << c;
         }
         if (!active) mask = 0;
-        // pass 1: the tile's survivors raise the k best screened scores (registers only)
+        // pass 1: the tile's survivors raise the k best screened scores
         for (uint64_t m1 = mask; m1; m1 &= m1 - 1) {
           const int c = __ffsll((long long)m1) - 1;
           const float a = av_s[c * kM + m];
-          if (a > ak && a >= cut) {
-            float v = a;
+          if constexpr (KMAX > 0) {
+            if (a > ak && a >= cut) {
+              float v = a;
 #pragma unroll
-            for (int j = 0; j < KMAX; ++j) {
-              if (j < k) {
-                const float hi = fmaxf(ta[j], v);
-                v = fminf(ta[j], v);
-                ta[j] = hi;
+              for (int j = 0; j < KMAX; ++j) {
+                if (j < k) {
+                  const float hi = fmaxf(ta[j], v);
+                  v = fminf(ta[j], v);
+                  ta[j] = hi;
+                }
               }
-            }
 #pragma unroll
-            for (int j = 0; j < KMAX; ++j)
-              if (j == k - 1) ak = ta[j];
+              for (int j = 0; j < KMAX; ++j)
+                if (j == k - 1) ak = ta[j];
+            }
+          } else {
+            if (hn < k) {                            // heap not full: sift the new score up
+              int j = hn++;
+              while (j > 0) {
+                const int par = (j - 1) >> 1;
+                const float pv = heap[par * kM];
+                if (pv <= a) break;
+                heap[j * kM] = pv;
+                j = par;
+              }
+              heap[j * kM] = a;
+              if (hn == k) ak = heap[0];
+            } else if (a > ak) {                     // replace the minimum, sift down
+              int j = 0;
+              for (;;) {
+                int ch = 2 * j + 1;
+                if (ch >= k) break;
+                float cv = heap[ch * kM];
+                if (ch + 1 < k) {
+                  const float c2 = heap[(ch + 1) * kM];
+                  if (c2 < cv) { cv = c2; ++ch; }
+                }
+                if (cv >= a) break;
+                heap[j * kM] = cv;
+                j = ch;
+              }
+              heap[j * kM] = a;
+              ak = heap[0];
+            }
           }
         }
         if (active && (i & 3) == 3) gq = fmaxf(gq, unordered(__ldcg(P.gbound + qid)) - dlt);
@@ -293,18 +346,31 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
           const int c = __ffsll((long long)mask) - 1;
           const float a = av_s[c * kM + m];
           if (a < cut) continue;
-          if (cnt == kCand) {                      // drop candidates that fell below the cut
-            int w = 0;
-            for (int j = 0; j < kCand; ++j)
-              if (cub[j * kM] >= cut) { cub[w * kM] = cub[j * kM]; cpos[w * kM] = cpos[j * kM]; ++w; }
-            cnt = w;
-          }
-          if (cnt < kCand) {
-            cub[cnt * kM] = a;
-            cpos[cnt * kM] = pr0 + c;
-            ++cnt;
+          if constexpr (KMAX > 0) {
+            if (cnt == kCand) {                      // drop candidates that fell below the cut
+              int w = 0;
+              for (int j = 0; j < kCand; ++j)
+                if (cub[j * kM] >= cut) { cub[w * kM] = cub[j * kM]; cpos[w * kM] = cpos[j * kM]; ++w; }
+              cnt = w;
+            }
+            if (cnt < kCand) {
+              cub[cnt * kM] = a;
+              cpos[cnt * kM] = pr0 + c;
+              ++cnt;
+            } else {
+              ovf = true;
+            }
           } else {
-            ovf = true;
+            if (cnt == P.kc) {                       // drop candidates that fell below the cut
+              int w = 0;
+              for (int j = 0; j < P.kc; ++j) {
+                const Cand v = glist[j];
+                if (v.s >= cut) glist[w++] = v;
+              }
+              cnt = w;
+            }
+            if (cnt < P.kc) glist[cnt++] = Cand{a, pr0 + c};
+            else ovf = true;
           }
         }
         __syncwarp();
@@ -312,10 +378,17 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
       }
       if (active && !abort_s) {
         const int64_t e = e0 + jq;
-        Cand* out = P.cand + e * kCand;
         int w = 0;
-        for (int j = 0; j < cnt; ++j)
-          if (cub[j * kM] >= cut) out[w++] = Cand{cub[j * kM] + dlt, cpos[j * kM]};   // upper bound of the exact score
+        if constexpr (KMAX > 0) {
+          Cand* out = P.cand + e * (int64_t)P.kc;
+          for (int j = 0; j < cnt; ++j)
+            if (cub[j * kM] >= cut) out[w++] = Cand{cub[j * kM] + dlt, cpos[j * kM]};   // upper bound of the exact score
+        } else {
+          for (int j = 0; j < cnt; ++j) {
+            const Cand v = glist[j];
+            if (v.s >= cut) glist[w++] = Cand{v.s + dlt, v.id};
+          }
+        }
         const float Lk = fmaxf(ak, floor_) - dlt;   // -inf while fewer than k rows were seen
         P.hdr[e] = make_int2(__float_as_int(Lk), w | (ovf ? (int)0x80000000 : 0));
         if (Lk > -INFINITY) atomicMax(P.gbound + qid, ordered(Lk));
@@ -343,13 +416,13 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
 }
 
 size_t smem_bytes(int kp, int k, int stages) {
-  return 1024 + (size_t)kM * kp * 4 + (size_t)stages * kN * kp * 4 + (size_t)kN * kM * 4 +
-         (size_t)kM * kCand * 8 + (size_t)(2 * stages + 4) * 8;
+  return 1024 + (size_t)kM * kp * 4 + (size_t)stages * kN * kp * 4 + (size_t)kN * kM * 4 + ext_bytes(k) +
+         (size_t)(2 * stages + 4) * 8;
 }
 
 int pick_stages(int kp, int k) {
   for (int s = kMaxStages; s >= 2; --s)
-    if (smem_bytes(kp, k, s) <= 220 * 1024) return s;
+    if (smem_bytes(kp, k, s) <= 227 * 1024) return s;
   return 0;
 }
 
@@ -472,6 +545,127 @@ __global__ void __launch_bounds__(256) rescore_lists(Cand* __restrict__ cand, co
   slot[lane] = Cand{s, id};
 }
 
+// Heap-mode counterpart of rescore_lists (32 < k <= 128, lists of kc <= 256
+// entries), a warp per (query, partition) slot: the candidates whose upper
+// bound reaches the query's bound are rescored exactly and the best k kept;
+// a slot whose list overflowed is rescanned exactly over its partition into
+// a shared-memory top-k list.  The slot is rewritten best first and closed
+// by a (-inf, -1) entry when shorter than kc.
+__global__ void __launch_bounds__(256) rescore_wide(Cand* __restrict__ cand, const int2* __restrict__ hdr, int64_t P,
+                                                    const int32_t* __restrict__ pair_vals, int t,
+                                                    const float* __restrict__ lstar, const float* __restrict__ Qf,
+                                                    int kp, const float* __restrict__ rows,
+                                                    const int32_t* __restrict__ ids,
+                                                    const int32_t* __restrict__ part_of_pair,
+                                                    const int64_t* __restrict__ gstart,
+                                                    const int64_t* __restrict__ part_off, int k, int kc,
+                                                    const int32_t* __restrict__ tpq) {
+  constexpr unsigned kFull = 0xffffffffu;
+  constexpr int R = kWideList / 32;       // candidates per lane
+  constexpr int U = kWideK / 32;          // top-k entries per lane
+  __shared__ Cand top_s[8][kWideK];
+  const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;   // uniform within a warp
+  const int lane = threadIdx.x & 31;
+  if (e >= P) return;
+  const int64_t q = pair_vals[e] / t;
+  const int j = pair_vals[e] - (int)(q * t);
+  if (tpq && j >= min(max(tpq[q], 1), t)) return;
+  const int2 h = hdr[e];
+  const int cnt = h.y & 0x7fffffff;
+  const bool ovf = h.y < 0;
+  const float bound = lstar[q];
+  const float* qv = Qf + q * (int64_t)kp;
+  Cand* slot = cand + e * (int64_t)kc;
+  if (!ovf) {
+    float v[R];
+    int id[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int idx = lane + 32 * r;
+      v[r] = -INFINITY;
+      id[r] = -1;
+      if (idx < cnt) {
+        const Cand c = slot[idx];
+        if (c.s >= bound) {
+          v[r] = exact_dot(qv, rows, kp, c.id);
+          id[r] = ids[c.id];
+        }
+      }
+    }
+    __syncwarp();
+    int out = 0;
+    for (; out < k; ++out) {
+      float bs = v[0];
+      int bid = id[0], br = 0;
+#pragma unroll
+      for (int r = 1; r < R; ++r)
+        if (better(v[r], id[r], bs, bid)) { bs = v[r]; bid = id[r]; br = r; }
+      float ws = bs;
+      int wid = bid, wl = lane;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float os = __shfl_xor_sync(kFull, ws, o);
+        const int oid = __shfl_xor_sync(kFull, wid, o);
+        const int ol = __shfl_xor_sync(kFull, wl, o);
+        if (better(os, oid, ws, wid) || (os == ws && oid == wid && ol < wl)) { ws = os; wid = oid; wl = ol; }
+      }
+      if (wid == -1) break;                  // every candidate taken
+      if (lane == wl) {
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+          if (r == br) { v[r] = -INFINITY; id[r] = -1; }
+      }
+      if (lane == 0) slot[out] = Cand{ws, wid};
+    }
+    if (lane == 0 && out < kc) slot[out] = Cand{-INFINITY, -1};
+    return;
+  }
+  // overflow: exact rescan of the partition
+  Cand* L = top_s[threadIdx.x >> 5];
+  for (int i = lane; i < k; i += 32) L[i] = Cand{-INFINITY, -1};
+  __syncwarp();
+  const int p = part_of_pair[e];
+  const int64_t r0 = gstart[p] * 8;
+  const int64_t nrows = part_off[p + 1] - part_off[p];
+  for (int64_t base = 0; base < nrows; base += 32) {
+    const int64_t r = base + lane;
+    float v = -INFINITY;
+    int rid = -1;
+    if (r < nrows) {
+      v = exact_dot(qv, rows, kp, r0 + r);
+      rid = ids[r0 + r];
+    }
+    unsigned ball = __ballot_sync(kFull, r < nrows && better(v, rid, L[k - 1].s, L[k - 1].id));
+    while (ball) {
+      const int src = __ffs(ball) - 1;
+      ball &= ball - 1;
+      const float vs = __shfl_sync(kFull, v, src);
+      const int is = __shfl_sync(kFull, rid, src);
+      if (!better(vs, is, L[k - 1].s, L[k - 1].id)) continue;   // same answer in every lane
+      int nb = 0;                                              // entries better than (vs, is)
+      for (int i = lane; i < k; i += 32) nb += better(L[i].s, L[i].id, vs, is) ? 1 : 0;
+      nb = __reduce_add_sync(kFull, nb);
+      Cand tmp[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = lane + 32 * u;
+        if (i >= nb && i < k - 1) tmp[u] = L[i];
+      }
+      __syncwarp();
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = lane + 32 * u;
+        if (i >= nb && i < k - 1) L[i + 1] = tmp[u];
+      }
+      __syncwarp();
+      if (lane == 0) L[nb] = Cand{vs, is};
+      __syncwarp();
+    }
+  }
+  for (int i = lane; i < k; i += 32) slot[i] = L[i];
+  if (lane == 0 && k < kc) slot[k] = Cand{-INFINITY, -1};
+}
+
 __global__ void fill_u32(unsigned* __restrict__ a, int64_t n, unsigned v) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) a[i] = v;
@@ -488,18 +682,21 @@ __global__ void pair_partitions(const int32_t* __restrict__ top, const int32_t* 
 
 int scan_tc_max_k(const IndexData& ix) {
   int k = 0;
-  while (k < kCand && pick_stages(ix.tc_kp, k + 1) >= 2) ++k;
+  while (k < kWideK && pick_stages(ix.tc_kp, k + 1) >= 2) ++k;
   return k;
 }
+
+int scan_tc_list_len(int k) { return list_len_for(k); }
 
 void scan_tc_search(const IndexData& ix, const IvfWork& work, int max_items, const float* Qf, const float* qnorm,
                     const int32_t* top, const int32_t* inv, const int32_t* tpq, int64_t nq, int t, int k,
                     Cand* lists, int* err, cudaStream_t s, Scratch& scr) {
   const int stages = pick_stages(ix.tc_kp, k);
-  if (stages < 2 || k > kCand) fail(SOAR_EUNSUPPORTED, "tensor-core scan: k too large");
+  if (stages < 2 || k > kWideK) fail(SOAR_EUNSUPPORTED, "tensor-core scan: k too large");
+  const int kc = list_len_for(k);
   const int64_t P = nq * t;
   int2* hdr = scr.get<int2>(P);
-  TcParams prm{work, ix.tc_rows, ix.tc_gstart, ix.tc_pmax, Qf, qnorm, ix.tc_kp, k, stages,
+  TcParams prm{work, ix.tc_rows, ix.tc_gstart, ix.tc_pmax, Qf, qnorm, ix.tc_kp, k, kc, stages,
                nullptr, err, nullptr, lists, hdr};
   prm.gbound = scr.get<unsigned>(nq);
   fill_u32<<<ceil_div(nq, 256), 256, 0, s>>>(prm.gbound, nq, 0x007fffffu);   // ordered key of -inf
@@ -507,7 +704,7 @@ void scan_tc_search(const IndexData& ix, const IvfWork& work, int max_items, con
   prm.counter = scr.get<int>(1);
   SOAR_CUDA(cudaMemsetAsync(prm.counter, 0, sizeof(int), s));
   const size_t smem = smem_bytes(ix.tc_kp, k, stages);
-  auto kern = k <= 16 ? scan_tc_kernel<16> : scan_tc_kernel<32>;
+  auto kern = k <= 16 ? scan_tc_kernel<16> : k <= kCand ? scan_tc_kernel<32> : scan_tc_kernel<0>;
   SOAR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int grid = std::max(1, std::min(max_items, num_sms()));
   stage_mark(s, "scan", true);
@@ -521,9 +718,14 @@ void scan_tc_search(const IndexData& ix, const IvfWork& work, int max_items, con
   int32_t* part = scr.get<int32_t>(P);
   pair_partitions<<<ceil_div(P, 256), 256, 0, s>>>(top, work.pair_vals, P, part);
   SOAR_LAUNCHED();
-  rescore_lists<<<ceil_div(P * 32, 256), 256, 0, s>>>(lists, hdr, P, work.pair_vals, t, lstar, Qf, ix.tc_kp,
-                                                      ix.tc_rows, ix.tc_ids, part, ix.tc_gstart, ix.offsets, k,
-                                                      tpq);
+  if (k <= kCand)
+    rescore_lists<<<ceil_div(P * 32, 256), 256, 0, s>>>(lists, hdr, P, work.pair_vals, t, lstar, Qf, ix.tc_kp,
+                                                        ix.tc_rows, ix.tc_ids, part, ix.tc_gstart, ix.offsets, k,
+                                                        tpq);
+  else
+    rescore_wide<<<ceil_div(P * 32, 256), 256, 0, s>>>(lists, hdr, P, work.pair_vals, t, lstar, Qf, ix.tc_kp,
+                                                       ix.tc_rows, ix.tc_ids, part, ix.tc_gstart, ix.offsets, k, kc,
+                                                       tpq);
   SOAR_LAUNCHED();
   stage_mark(s, "rescore", false);
 }

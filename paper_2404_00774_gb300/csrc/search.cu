@@ -871,7 +871,7 @@ void search(const IndexData& ix, const void* Q, soar_dtype dt, int64_t nq, int32
     stage_mark(s, "select", false);
     const int64_t P = nq * t;
     int32_t* inv = scr.get<int32_t>(P);
-    const int len = scan_tc_list_len();
+    const int len = scan_tc_list_len(k);
     Cand* lists = scr.get<Cand>((size_t)P * len);
     Grouped g = group_pairs(ix, nq, t, tpq, 128, top, inv, s, scr);
     IvfWork work{ix.offsets, g.pair_off, g.vals, ix.part_order, g.item_base, ix.c, t, 128};

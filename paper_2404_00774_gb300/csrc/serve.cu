@@ -2,10 +2,14 @@
 // paper describes no serving system).
 //
 // Requests (one fp32 query, its own k and t) are queued by soar_server_submit
-// from any thread.  A dispatcher thread keeps up to `streams` batches in
-// flight: whenever a stream slot is free it takes pending requests in arrival
-// order, admitting each while the batch stays within max_batch and the
-// device-memory estimate of everything in flight stays within the budget;
+// from any thread, or as a trace of timed arrivals by soar_server_submit_many
+// (a request becomes pending at its arrival time, and its latency counts from
+// then).  A dispatcher thread keeps up to `streams` batches in flight:
+// whenever a stream slot is free it takes pending requests in arrival order,
+// keeping to one k class per batch (k <= 32 or k > 32, which the search
+// serves with different list structures), admitting each while the batch
+// stays within max_batch and the device-memory estimate of everything in
+// flight stays within the budget;
 // the batch then runs on that slot's stream (host-to-device copy of the
 // queries, one soar_search with per-request probe counts and the batch's
 // largest k, device-to-host copy of the results).  Requests that arrive while
@@ -15,8 +19,10 @@
 // top-k' list for k <= k').
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
@@ -72,6 +78,7 @@ struct soar_server {
   std::condition_variable cv_work;   // dispatcher: new request or slot freed
   std::condition_variable cv_done;   // waiters: a request completed
   std::deque<Request> pending;
+  std::multimap<Clock::time_point, Request> scheduled;   // future arrivals of submit_many
   std::unordered_map<uint64_t, Done> finished;
   uint64_t next_id = 1;
   size_t in_flight_bytes = 0;
@@ -120,11 +127,19 @@ void CUDART_CB batch_done(void* arg) {
   sv->cv_work.notify_one();
 }
 
+int k_class(int k) { return k <= 32 ? 0 : 1; }
+
 void dispatcher(soar_server* sv) {
   cudaSetDevice(sv->device);
   const soar::IndexData& ix = sv->index->data;
   std::unique_lock<std::mutex> lock(sv->mu);
   while (true) {
+    // scheduled requests whose arrival time has come become pending
+    const auto now = Clock::now();
+    while (!sv->scheduled.empty() && sv->scheduled.begin()->first <= now) {
+      sv->pending.push_back(std::move(sv->scheduled.begin()->second));
+      sv->scheduled.erase(sv->scheduled.begin());
+    }
     // retire finished batches
     int busy = 0;
     for (Slot& sl : sv->slots) {
@@ -132,7 +147,7 @@ void dispatcher(soar_server* sv) {
       if (cudaEventQuery(sl.done) == cudaSuccess) finish_slot(sv, sl);
       else ++busy;
     }
-    if (busy == 0 && sv->stop && sv->pending.empty()) break;
+    if (busy == 0 && sv->stop && sv->pending.empty() && sv->scheduled.empty()) break;
     sv->cv_done.notify_all();
     // launch a batch into a free slot
     Slot* free_slot = nullptr;
@@ -141,14 +156,25 @@ void dispatcher(soar_server* sv) {
     if (free_slot && !sv->pending.empty()) {
       Slot& sl = *free_slot;
       size_t bytes = 0;
+      const int cls = k_class(sv->pending.front().k);
+      std::deque<Request> skipped;                 // other k class: stays pending, in order
       while (!sv->pending.empty() && (int)sl.batch.size() < sv->cfg.max_batch) {
         const Request& r = sv->pending.front();
+        if (k_class(r.k) != cls) {
+          skipped.push_back(std::move(sv->pending.front()));
+          sv->pending.pop_front();
+          continue;
+        }
         // the first request of a batch is always admitted when nothing else runs
         const bool fits = sv->in_flight_bytes + bytes + r.bytes <= (size_t)sv->cfg.memory_budget;
         if (!fits && !(sl.batch.empty() && busy == 0)) break;
         bytes += r.bytes;
         sl.batch.push_back(std::move(sv->pending.front()));
         sv->pending.pop_front();
+      }
+      while (!skipped.empty()) {
+        sv->pending.push_front(std::move(skipped.back()));
+        skipped.pop_back();
       }
       if (!sl.batch.empty()) {
         const int nb = (int)sl.batch.size();
@@ -182,8 +208,11 @@ void dispatcher(soar_server* sv) {
         continue;   // look for more work right away
       }
     }
-    // nothing to launch: sleep until a request arrives or a batch completes
-    sv->cv_work.wait_for(lock, std::chrono::milliseconds(2));
+    // nothing to launch: sleep until a request arrives, a batch completes or
+    // the next scheduled arrival is due
+    auto until = Clock::now() + std::chrono::milliseconds(2);
+    if (!sv->scheduled.empty()) until = std::min(until, sv->scheduled.begin()->first);
+    sv->cv_work.wait_until(lock, until);
   }
   sv->cv_done.notify_all();
 }
@@ -247,6 +276,70 @@ soar_status soar_server_submit(soar_server* sv, const float* query, int32_t k, i
   return SOAR_OK;
 }
 
+soar_status soar_server_submit_many(soar_server* sv, const float* queries, int64_t n, const int32_t* ks,
+                                   const int32_t* ts, const double* arrival_s, uint64_t* request_ids) {
+  if (!sv || n < 0 || (n > 0 && (!queries || !ks || !ts || !request_ids))) return SOAR_EINVAL;
+  const soar::IndexData& ix = sv->index->data;
+  for (int64_t i = 0; i < n; ++i) {
+    if (ks[i] < 1 || ks[i] > sv->cfg.max_k || ts[i] < 1 || ts[i] > ix.c || ts[i] > 8192) return SOAR_EINVAL;
+    if (arrival_s && !(arrival_s[i] >= 0.0 && arrival_s[i] < 1e6)) return SOAR_EINVAL;
+  }
+  const auto t0 = Clock::now();
+  std::vector<Request> reqs((size_t)n);
+  for (int64_t i = 0; i < n; ++i) {
+    Request& r = reqs[(size_t)i];
+    r.q.assign(queries + i * ix.d, queries + (i + 1) * ix.d);
+    r.k = ks[i];
+    r.t = ts[i];
+    r.bytes = request_bytes(ix, r.k, r.t);
+    r.submitted = arrival_s ? t0 + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(arrival_s[i]))
+                            : t0;
+  }
+  {
+    std::lock_guard<std::mutex> lock(sv->mu);
+    if (sv->stop) return SOAR_EINVAL;
+    for (int64_t i = 0; i < n; ++i) {
+      Request& r = reqs[(size_t)i];
+      r.id = sv->next_id++;
+      request_ids[i] = r.id;
+      if (arrival_s) sv->scheduled.emplace(r.submitted, std::move(r));
+      else sv->pending.push_back(std::move(r));
+    }
+  }
+  sv->cv_work.notify_one();
+  return SOAR_OK;
+}
+
+soar_status soar_server_wait_many(soar_server* sv, const uint64_t* request_ids, int64_t n, int32_t kstride,
+                                  int64_t* ids_out, float* scores_out, double* latency_ms, int32_t timeout_ms) {
+  if (!sv || n < 0 || kstride < 1 || (n > 0 && (!request_ids || !ids_out || !scores_out))) return SOAR_EINVAL;
+  std::unique_lock<std::mutex> lock(sv->mu);
+  const auto deadline = Clock::now() + std::chrono::milliseconds(timeout_ms);
+  soar_status worst = SOAR_OK;
+  for (int64_t i = 0; i < n; ++i) {
+    const uint64_t id = request_ids[i];
+    if (id == 0 || id >= sv->next_id) return SOAR_EINVAL;
+    while (true) {
+      auto it = sv->finished.find(id);
+      if (it != sv->finished.end()) {
+        Done d = std::move(it->second);
+        sv->finished.erase(it);
+        const size_t kk = std::min(d.ids.size(), (size_t)kstride);
+        std::copy(d.ids.begin(), d.ids.begin() + kk, ids_out + i * kstride);
+        std::copy(d.scores.begin(), d.scores.begin() + kk, scores_out + i * kstride);
+        std::fill(ids_out + i * kstride + kk, ids_out + (i + 1) * kstride, int64_t(-1));
+        std::fill(scores_out + i * kstride + kk, scores_out + (i + 1) * kstride, -INFINITY);
+        if (latency_ms) latency_ms[i] = d.latency_ms;
+        if (d.status != SOAR_OK) worst = d.status;
+        break;
+      }
+      if (sv->cv_done.wait_until(lock, deadline) == std::cv_status::timeout && Clock::now() >= deadline)
+        return SOAR_ETIMEOUT;
+    }
+  }
+  return worst;
+}
+
 soar_status soar_server_wait(soar_server* sv, uint64_t request_id, int64_t* ids_out, float* scores_out,
                              double* latency_ms, int32_t timeout_ms) {
   if (!sv || !ids_out || !scores_out) return SOAR_EINVAL;
@@ -274,7 +367,7 @@ soar_status soar_server_stats(soar_server* sv, soar_server_metrics* out) {
   out->batches = sv->batches;
   out->completed = sv->completed;
   out->queries_in_batches = sv->queries_in_batches;
-  out->pending = sv->pending.size();
+  out->pending = sv->pending.size() + sv->scheduled.size();
   out->max_in_flight = sv->max_in_flight;
   std::vector<double> lat = sv->latencies;
   std::sort(lat.begin(), lat.end());

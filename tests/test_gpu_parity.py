@@ -235,6 +235,46 @@ def test_search_equal_rows_overflow_candidate_lists(soar):
     ix.close()
 
 
+@pytest.mark.parametrize("k,t", [(33, 4), (64, 17), (128, 6)])
+def test_search_wide_k_matches_oracle(soar, tiny_index, k, t):
+    # k above 32: per-query heaps of screened scores, global candidate lists
+    X, Q, C, A, off, ids, ix = tiny_index
+    tpq = np.random.default_rng(k).integers(1, t + 1, size=Q.shape[0]).astype(np.int32)
+    for per_query in (None, tpq):
+        gi, gs = soar.soar_search(ix, _t(Q), k, t, t_per_query=None if per_query is None else _t(per_query))
+        wi, ws = oracle.ivf_search(Q, X, C, off, ids, k, t, t_per_query=per_query)
+        gi, gs = gi.cpu().numpy(), gs.cpu().numpy()
+        ex = _exact(X, Q)
+        assert topk_mismatches(gi, wi, ws, ex) == [], k
+        np.testing.assert_array_equal(gi < 0, wi < 0)
+        mx, _ = score_errors(gi, gs, ex)
+        assert mx < 1e-5
+
+
+def test_search_wide_k_overflow_rescans_partition(soar):
+    # 400 identical rows tie exactly: more candidates than a 224-entry list
+    # holds for k = 100, so the exact rescan of the partition decides
+    rng = np.random.default_rng(37)
+    X = rng.standard_normal((4000, 24)).astype(np.float32)
+    X /= np.linalg.norm(X, axis=1, keepdims=True)
+    X[500:900] = X[500]
+    Q = rng.standard_normal((12, 24)).astype(np.float32)
+    Q[:5] = X[500] + 0.02 * rng.standard_normal((5, 24)).astype(np.float32)
+    Q /= np.linalg.norm(Q, axis=1, keepdims=True)
+    C = oracle.kmeans(X, rng.choice(4000, 8, replace=False), 3)
+    A = oracle.soar_assign(X, C, 1.0, 1)
+    off, ids = oracle.build_ivf(A, 8)
+    ix = soar.soar_index_build(_t(X), _t(C), _t(A))
+    for k, t in [(100, 1), (100, 3), (128, 2)]:
+        gi, gs = soar.soar_search(ix, _t(Q), k, t)
+        wi, ws = oracle.ivf_search(Q, X, C, off, ids, k, t)
+        gi = gi.cpu().numpy()
+        assert topk_mismatches(gi, wi, ws, _exact(X, Q)) == [], (k, t)
+        np.testing.assert_array_equal(gi[:5], wi[:5])     # ties go to the lower ids
+    soar.soar_check_device()
+    ix.close()
+
+
 def test_search_bf16_index(soar, tiny):
     X, Q, init, C = tiny
     Xb = oracle.bf16_round(X)

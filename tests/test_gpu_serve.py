@@ -64,6 +64,31 @@ def test_results_equal_alone_and_in_a_concurrent_mix(soar, served):
     srv.close()
 
 
+def test_replayed_arrivals_match_alone_results(soar, served):
+    X, Q, ix = served
+    n = len(Q)
+    rng = np.random.default_rng(21)
+    ks = rng.choice([10, 40, 100], size=n).astype(np.int32)
+    ts = rng.integers(1, 17, size=n).astype(np.int32)
+    arrivals = np.sort(rng.uniform(0.0, 0.05, size=n))       # a 50 ms trace
+    srv = soar.Server(ix, max_batch=64, streams=3, memory_budget=1 << 28, max_k=100)
+    rids = srv.submit_many(Q, ks, ts, arrival_s=arrivals)
+    ids, sc, lat = srv.wait_many(rids, 100)
+    Xd, Qd = X.astype(np.float64), Q.astype(np.float64)
+    for i in range(n):
+        want_ids, want_sc = _alone(soar, ix, Q[i], int(ks[i]), int(ts[i]))
+        ex = lambda q, v: Xd[np.asarray(v, np.int64)] @ Qd[i]
+        got = ids[i, :ks[i]]
+        assert topk_mismatches(got[None], want_ids[None], want_sc[None].astype(np.float64), ex) == [], i
+        assert np.all(ids[i, ks[i]:] == -1) and np.all(np.isneginf(sc[i, ks[i]:]))
+    assert np.all(lat > 0)
+    st = srv.stats()
+    assert st["completed"] == n and st["pending"] == 0
+    with pytest.raises(soar.SoarError):
+        srv.submit_many(Q[:2], [10, 101], [4, 4])          # one bad k rejects the call
+    srv.close()
+
+
 def test_batches_overlap_on_the_gpu(soar, served):
     X, Q, ix = served
     srv = soar.Server(ix, max_batch=16, streams=4, memory_budget=1 << 30, max_k=10)
