@@ -296,6 +296,11 @@ void assign_typed(const XT* X, int64_t n, int32_t d, const float* C, int32_t c, 
       residual_kernel<XT><<<wgrid, 256, 0, s>>>(X, n, d, C, assign, astride, j - 1, inv_rn, xr);
       SOAR_LAUNCHED();
     }
+    if (assign_tc_supported(d, j)) {
+      // primary and first spill: tensor-core screen with rigorous bounds
+      assign_tc_pass<XT>(X, n, d, C, c, j, assign, astride, inv_rn, lambda, s, scr);
+      continue;
+    }
     screen_launch<XT>(j, X, n, d, C, cnorm, c, assign, astride, inv_rn, xr, lambda, cand, s);
     refine_kernel<XT><<<wgrid, 256, 0, s>>>(X, n, d, C, assign, astride, j, lambda, cand);
     SOAR_LAUNCHED();

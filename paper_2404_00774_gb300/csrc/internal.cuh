@@ -38,6 +38,14 @@ void assign_points(const void* X, soar_dtype dt, int64_t n, int32_t d, const flo
 void kmeans_train(const void* X, soar_dtype dt, int64_t n, int32_t d, int32_t c, int32_t iters,
                   const int32_t* init_idx, float* C, cudaStream_t s, Scratch& scr);
 
+// Tensor-core assignment pass (assign_tc.cu): the primary assignment
+// (ndir = 0) or the first spill (ndir = 1, inv_rn[n][4] column 0 from the
+// residual kernel), written to column ndir of assign[n][astride].
+bool assign_tc_supported(int d, int ndir);
+template <typename XT>
+void assign_tc_pass(const XT* X, int64_t n, int d, const float* C, int c, int ndir, int32_t* assign, int astride,
+                    const float* inv_rn, float lambda, cudaStream_t s, Scratch& scr);
+
 // ----------------------------------------------------------- ivf.cu
 
 struct IndexData {

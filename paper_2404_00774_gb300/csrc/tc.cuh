@@ -43,6 +43,19 @@ __device__ __forceinline__ bool bar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
+// try_wait with a suspend-time hint: the thread sleeps in hardware until the
+// phase completes or about `ns` nanoseconds passed, instead of spinning on
+// issue slots the other warps need.
+__device__ __forceinline__ bool bar_try_wait_sleep(uint32_t bar, uint32_t parity, uint32_t ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
+
 // Waits for the phase of `parity` to complete, at most ~2^31 SM cycles (about
 // a second); gives up early when *abort becomes non-zero.  Returns false when
 // it gave up.
@@ -55,6 +68,30 @@ __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, volatile
   return true;
 }
 
+// bar_wait for roles that may wait long (producer, MMA issuer, epilogue):
+// each poll suspends the thread for up to a microsecond.
+__device__ __forceinline__ bool bar_wait_sleep(uint32_t bar, uint32_t parity, volatile int* abort) {
+  const long long t0 = clock64();
+  while (!bar_try_wait_sleep(bar, parity, 1000u)) {
+    if (*abort) return false;
+    if (clock64() - t0 > (1ll << 31)) return false;
+  }
+  return true;
+}
+
+// Named barrier `id` over `count` threads (whole warps) that also ORs a
+// predicate across them.  Unlike an mbarrier access, it does not stall a
+// thread that has tcgen05.mma instructions in flight.
+__device__ __forceinline__ bool named_bar_or(uint32_t id, uint32_t count, bool pred) {
+  uint32_t out;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}"
+      : "=r"(out)
+      : "r"((uint32_t)pred), "r"(id), "r"(count)
+      : "memory");
+  return out != 0;
+}
+
 // ------------------------------------------------------------------ copies
 
 // Contiguous global -> shared copy completing on `bar` (16-byte aligned
@@ -65,6 +102,13 @@ __device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void* src, uin
       "l"(src), "r"(bytes), "r"(bar)
       : "memory");
 }
+
+// 16-byte asynchronous global -> shared copy (both addresses 16-byte aligned),
+// completed by cp_async_wait_all in the issuing thread.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Makes this thread's ordinary shared-memory stores visible to the tensor core.
 __device__ __forceinline__ void fence_async_smem() {

@@ -107,6 +107,58 @@ def test_soar_assign_ragged_and_degenerate(soar):
     assert np.all(np.sort(got, axis=1) == [0, 1])
 
 
+def test_soar_assign_many_tied_centroids(soar):
+    # 21 identical centroids tie exactly for the points around them: more
+    # candidates than the tensor-core screen keeps, so those points are
+    # decided by scoring every centroid, and the lowest index must win
+    rng = np.random.default_rng(41)
+    n, d, c = 700, 24, 90
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    C = rng.standard_normal((c, d)).astype(np.float32)
+    C[20:40] = C[5]
+    X[:200] = C[5] + 0.05 * rng.standard_normal((200, d)).astype(np.float32)
+    for lam, s in [(0.0, 0), (1.0, 1), (0.0, 1)]:
+        got = soar.soar_assign(_t(X), _t(C), lam, s).cpu().numpy()
+        want, gaps, best = oracle.soar_assign(X, C, lam, s, return_gaps=True)
+        bad, _ = assign_mismatches(got, want, gaps, best)
+        assert len(bad) == 0, (lam, s, bad[:5])
+        assert np.all(got[:200, 0] == 5)
+        if s:
+            assert np.all(got[:200, 1] == 20)
+
+
+def test_soar_assign_glove_shaped_slice(soar):
+    # d = 100 (the Glove shape): many 128-point tiles, several centroid tiles
+    w = synth.WORKLOADS["glove"]
+    mix = synth.mixture_for(w)
+    X = mix.sample(12_000, 7)
+    C = X[synth.init_indices(12_000, 256, 8)].copy()
+    for lam, s in [(1.0, 1), (0.0, 0)]:
+        got = soar.soar_assign(_t(X), _t(C), lam, s).cpu().numpy()
+        want, gaps, best = oracle.soar_assign(X, C, lam, s, return_gaps=True)
+        bad, _ = assign_mismatches(got, want, gaps, best)
+        assert len(bad) == 0, (lam, s, bad[:5])
+
+
+def test_soar_assign_unaligned_rows(soar):
+    # a row pointer 4 bytes past a 16-byte boundary takes the element-wise
+    # staging path; the result must not change
+    rng = np.random.default_rng(43)
+    n, d, c = 900, 32, 40
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    C = rng.standard_normal((c, d)).astype(np.float32)
+    flat = torch.zeros(n * d + 1, dtype=torch.float32, device=DEV)
+    flat[1:] = _t(X).reshape(-1)
+    Xu = flat[1:].view(n, d)
+    assert Xu.data_ptr() % 16 == 4
+    for lam, s in [(1.0, 1), (0.0, 0)]:
+        got = soar.soar_assign(Xu, _t(C), lam, s).cpu().numpy()
+        np.testing.assert_array_equal(got, soar.soar_assign(_t(X), _t(C), lam, s).cpu().numpy())
+        want, gaps, best = oracle.soar_assign(X, C, lam, s, return_gaps=True)
+        bad, _ = assign_mismatches(got, want, gaps, best)
+        assert len(bad) == 0
+
+
 def test_fig3_worked_example_on_gpu(soar):
     x = np.array([[2.8, 1.9]], dtype=np.float32)
     C = np.array([[2.0, 2.5], [1.68, 2.74], [3.01, 0.24]], dtype=np.float32)
