@@ -24,8 +24,11 @@
 // upper bound reaches it and rescans exactly any partition whose candidate
 // list overflowed, so the final lists equal those of an exact scan.
 //
-// Warp roles: 0 = bulk-copy producer, 1 = TMEM owner and MMA issuer,
-// 2..5 = epilogue (query slot = 32 * (warp % 4) + lane, its TMEM lane).
+// Warp roles: 0 = bulk-copy producer (it also claims and resolves the next
+// work item ahead and prefetches its first tiles into L2), 1 = TMEM owner and
+// MMA issuer, 2 = gate (does the mbarrier waits for the MMA issuer), 3..6 =
+// epilogue (query slot = 32 * (warp % 4) + lane, its TMEM lane).  A stage of
+// the tile ring is released by the MMA's completion, not by the epilogue.
 // Every mbarrier wait is bounded (about a second); on expiry the CTA raises
 // *err, stops taking work, waits (bounded) for its copies and MMAs in flight,
 // frees its TMEM and returns.
@@ -38,7 +41,7 @@ namespace {
 
 constexpr int kM = 128;        // query slots per item (MMA M)
 constexpr int kN = 64;         // rows per tile (MMA N)
-constexpr int kThreads = 192;  // 6 warps
+constexpr int kThreads = 224;  // producer, MMA issuer, gate, 4 epilogue warps
 constexpr int kMaxStages = 4;
 constexpr int kCand = 32;      // candidate rows kept per (query, partition), register mode
 constexpr int kWideK = 128;    // largest k of the heap mode
@@ -82,6 +85,28 @@ __device__ __forceinline__ float unordered(unsigned k) {
   return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
 }
 
+// A work item resolved: partition p (-1: no more items), its first pair slot
+// and query count, its row count, first 8-row group and group count.
+struct ItemDesc {
+  int p, nqi, nrows, ng;
+  int64_t e0, g0;
+};
+
+__device__ ItemDesc describe_item(const TcParams& P, int item, int total) {
+  ItemDesc d{};
+  d.p = -1;
+  if (item >= total) return d;
+  const int oi = P.work.partition_of(item);
+  const int p = P.work.order[oi];
+  d.p = p;
+  d.e0 = P.work.pair_off[p] + (int64_t)(item - P.work.item_base[oi]) * kM;
+  d.nqi = (int)min((int64_t)kM, P.work.pair_off[p + 1] - d.e0);
+  d.nrows = (int)(P.work.part_off[p + 1] - P.work.part_off[p]);
+  d.g0 = P.gstart[p];
+  d.ng = (int)(P.gstart[p + 1] - d.g0);
+  return d;
+}
+
 template <int KMAX>
 __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -94,16 +119,17 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
   const uint32_t b_bytes = (uint32_t)kN * kp * 4u;
   float* sA = reinterpret_cast<float*>(base);
   float* sB = reinterpret_cast<float*>(base + a_bytes);
-  float* av_s = reinterpret_cast<float*>(base + a_bytes + (size_t)S * b_bytes);  // [kN][kM] tile scores
+  float* av_s = reinterpret_cast<float*>(base + a_bytes + (size_t)S * b_bytes);  // [kN][kM] parked scores
   // per-slot arrays are interleaved slot-fastest ([entry][kM]) so that the 32
   // lanes of a warp always touch 32 distinct banks
   float* ext_s = av_s + kN * kM;   // candidates [kCand][kM] (+ rows) or the heap [k][kM]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(ext_s) + ext_bytes(k));
+  float* qn_s = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(ext_s) + ext_bytes(k));  // [kM]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(qn_s + kM);
   // bars: full[S], empty[S], tfull[2], tempty[2]
   __shared__ uint32_t tmem_base_s;
-  __shared__ int item_s;
+  __shared__ ItemDesc item_s;
   __shared__ int abort_s;
-  __shared__ int issued_s, consumed_s, mma_issued_s;
+  __shared__ int issued_s, consumed_s, committed_s;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   auto full = [&](int s) { return tc::smem_u32(&bars[s]); };
@@ -114,7 +140,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       tc::bar_init(full(s), 1);
-      tc::bar_init(empty(s), 4);
+      tc::bar_init(empty(s), 1);
     }
     for (int b = 0; b < 2; ++b) {
       tc::bar_init(tfull(b), 1);
@@ -122,7 +148,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
     }
     tc::bar_init_fence();
     abort_s = 0;
-    issued_s = consumed_s = mma_issued_s = 0;
+    issued_s = consumed_s = committed_s = 0;
   }
   if (warp == 1) tc::tmem_alloc(tc::smem_u32(&tmem_base_s), 2 * kN);
   tc::fence_before_sync();
@@ -134,31 +160,38 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
   auto give_up = [&]() {
     if (atomicExch(&abort_s, 1) == 0) atomicExch(P.err, 1);
   };
+  // epilogue thread: the TMEM lane quarter of warp % 4 holds query slot m;
+  // it takes the item's query j = 4 * lane + warp % 4, so that the active
+  // queries spread evenly over the four epilogue warps
+  const int m = 32 * (warp & 3) + lane;
+  const int jq = 4 * lane + (warp & 3);
 
-  uint32_t tile_ctr = 0;
+  uint32_t tile_ctr = 0, committed = 0;
   const int total = P.work.count();
+  // The producer thread claims items one ahead and resolves the next item's
+  // description (a chain of dependent global loads: a binary search over the
+  // item table, then the partition's offsets) while the current item runs;
+  // the other threads read it from shared memory at the item boundary.
+  ItemDesc next{};
+  if (threadIdx.x == 0) next = describe_item(P, atomicAdd(P.counter, 1), total);
   for (;;) {
-    if (threadIdx.x == 0) item_s = abort_s ? total : atomicAdd(P.counter, 1);
+    if (threadIdx.x == 0) {
+      item_s = next;
+      if (abort_s) item_s.p = -1;
+    }
     __syncthreads();
-    const int item = item_s;
-    if (item >= total) break;
-    const int oi = P.work.partition_of(item);
-    const int p = P.work.order[oi];
-    const int64_t e0 = P.work.pair_off[p] + (int64_t)(item - P.work.item_base[oi]) * kM;
-    const int nqi = (int)min((int64_t)kM, P.work.pair_off[p + 1] - e0);
-    const int64_t row0 = P.work.part_off[p];
-    const int nrows = (int)(P.work.part_off[p + 1] - row0);
-    const int64_t g0 = P.gstart[p];
-    const int ng = (int)(P.gstart[p + 1] - g0);
+    const ItemDesc D = item_s;
+    if (D.p < 0) break;
+    const int p = D.p;
+    const int64_t e0 = D.e0;
+    const int nqi = D.nqi;
+    const int nrows = D.nrows;
+    const int64_t g0 = D.g0;
+    const int ng = D.ng;
     const int ntiles = (ng + 7) / 8;
 
-    // ---- queries of the item -> A operand.  The thread owning TMEM lane m =
-    // 32 * (warp % 4) + lane takes the item's query j = 4 * lane + warp % 4,
-    // so the active queries spread evenly over the four epilogue warps.
-    const int m = 32 * (warp & 3) + lane;     // A row / TMEM lane of this thread
-    const int jq = 4 * lane + (warp & 3);     // the item's query held in that row
-    float qn = 0.f;
-    if (warp >= 2) {
+    // ---- queries of the item -> A operand (row m of the epilogue threads)
+    if (warp >= 3) {
       const bool active = jq < nqi;
       const float* q = active ? P.Qf + P.work.query(e0 + jq) * (int64_t)kp : nullptr;
       float* arow = sA + (m >> 3) * (kp * 8) + (m & 7) * 4;
@@ -166,60 +199,73 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
         float4 v = active ? *reinterpret_cast<const float4*>(q + 4 * k4) : make_float4(0.f, 0.f, 0.f, 0.f);
         *reinterpret_cast<float4*>(arow + k4 * 32) = v;
       }
-      if (active) qn = P.qnorm[P.work.query(e0 + jq)];
+      qn_s[m] = active ? P.qnorm[P.work.query(e0 + jq)] : 0.f;
       tc::fence_async_smem();
     }
     __syncthreads();
 
     if (warp == 0) {
-      // ---- producer: one thread streams the partition's tiles
+      // ---- producer: one thread streams the partition's tiles, keeping the
+      // tiles S ahead of the copies in flight prefetched into L2
       if (lane == 0) {
+        auto tile_bytes = [&](int ngr, int t) { return (uint32_t)min(8, ngr - 8 * t) * 8u * kp * 4u; };
+        for (int i = 0; i < min(S, ntiles); ++i)
+          tc::bulk_prefetch_l2(P.rows + (g0 + 8 * i) * 8 * kp, tile_bytes(ng, i));
         for (int i = 0; i < ntiles; ++i) {
           const uint32_t T = tile_ctr + i, s = T % S, ph = (T / S) & 1;
+          if (i + S < ntiles) tc::bulk_prefetch_l2(P.rows + (g0 + 8 * (i + S)) * 8 * kp, tile_bytes(ng, i + S));
           if (!tc::bar_wait(empty(s), ph ^ 1, abort_v)) { give_up(); break; }
-          const int groups = min(8, ng - 8 * i);
-          const uint32_t bytes = (uint32_t)groups * 8u * kp * 4u;
-          const int64_t pr0 = (g0 + 8 * i) * 8;
+          const uint32_t bytes = tile_bytes(ng, i);
           tc::bar_arrive_expect_tx(full(s), bytes);
-          tc::bulk_copy_g2s(tc::smem_u32(sB) + s * b_bytes, P.rows + pr0 * kp, bytes, full(s));
+          tc::bulk_copy_g2s(tc::smem_u32(sB) + s * b_bytes, P.rows + (g0 + 8 * i) * 8 * kp, bytes, full(s));
           issued_s = (int)(T + 1);
         }
+        // claim the next item, resolve it and warm L2 with its first tiles
+        next = describe_item(P, atomicAdd(P.counter, 1), total);
+        if (next.p >= 0)
+          for (int i = 0; i < min(S, (next.ng + 7) / 8); ++i)
+            tc::bulk_prefetch_l2(P.rows + (next.g0 + 8 * i) * 8 * kp, tile_bytes(next.ng, i));
       }
     } else if (warp == 1) {
-      // ---- MMA issuer
-      if (lane == 0) {
-        for (int i = 0; i < ntiles; ++i) {
-          const uint32_t T = tile_ctr + i, s = T % S, ph = (T / S) & 1, b = T & 1, tph = (T >> 1) & 1;
-          if (!tc::bar_wait(full(s), ph, abort_v)) { give_up(); break; }
-          consumed_s = (int)(T + 1);
-          if (!tc::bar_wait(tempty(b), tph ^ 1, abort_v)) { give_up(); break; }
+      // ---- MMA issuer.  It never touches an mbarrier (an mbarrier access
+      // right after tcgen05.mma stalls the thread until the MMAs drain): the
+      // gate warp waits for it and hands each tile over through a named
+      // barrier that also carries the stop flag.
+      for (int i = 0; i < ntiles; ++i) {
+        if (tc::named_bar_or(2, 64, false)) break;
+        const uint32_t T = tile_ctr + i, s = T % S, b = T & 1;
+        if (lane == 0) {
           tc::fence_after_sync();
           const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB) + s * b_bytes;
           for (int j = 0; j < kp / 8; ++j)
             tc::mma_tf32(tmem + b * kN, tc::smem_desc(a0 + j * 256, 128, sbo), tc::smem_desc(b0 + j * 256, 128, sbo),
                          idesc, j > 0);
+          tc::mma_commit(empty(s));                  // the stage is free once these MMAs completed
           tc::mma_commit(tfull(b));
-          mma_issued_s = (int)(T + 1);
         }
+        __syncwarp();
+        committed = T + 1;
+      }
+      if (lane == 0) committed_s = (int)committed;
+    } else if (warp == 2) {
+      // ---- gate: waits for each tile's stage and TMEM buffer, then releases
+      // the MMA issuer
+      for (int i = 0; i < ntiles; ++i) {
+        const uint32_t T = tile_ctr + i, s = T % S, ph = (T / S) & 1, b = T & 1, tph = (T >> 1) & 1;
+        int ok = 1;
+        if (lane == 0) {
+          ok = tc::bar_wait(full(s), ph, abort_v) && tc::bar_wait(tempty(b), tph ^ 1, abort_v);
+          if (!ok) give_up();
+          else consumed_s = (int)(T + 1);
+          tc::fence_before_sync();
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (tc::named_bar_or(2, 64, !ok)) break;
       }
     } else {
       // ---- epilogue: screening bounds and candidate rows per query
       const bool active = jq < nqi;
-      // register mode (KMAX > 0): the k best screened scores in registers and
-      // up to kCand candidates in shared memory.  Heap mode (KMAX == 0): the
-      // k best screened scores in a shared-memory min-heap and up to kc
-      // candidates in the slot's global list.
-      float ta[KMAX > 0 ? KMAX : 1];
-#pragma unroll
-      for (int j = 0; j < (KMAX > 0 ? KMAX : 1); ++j) ta[j] = -INFINITY;
-      float* cub = ext_s + m;                       // register mode: [kCand][kM] scores
-      int32_t* cpos = reinterpret_cast<int32_t*>(ext_s + kM * kCand) + m;   // [kCand][kM] padded rows
-      float* heap = ext_s + m;                      // heap mode: [k][kM]
-      int hn = 0;                                   // heap fill
-      const int64_t eslot = e0 + (active ? jq : 0);
-      Cand* glist = P.cand + eslot * (int64_t)P.kc;  // heap mode: candidates in global memory
-      int cnt = 0;
-      bool ovf = false;
+      const float qn = qn_s[m];
       const float dlt = ldexpf(qn, -8) * P.pmax[p];   // |s~ - exact| < dlt / 2 for every row of p
       // G_q, published by this query's finished partitions, bounds its final
       // k-th best exact score from below: rows with s~ + dlt < G_q cannot count
@@ -228,23 +274,39 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
       float ak = -INFINITY;                            // k-th best screened score (-inf until k seen)
       float floor_ = -INFINITY;                        // a lower bound of the k-th best screened score
       float cut = gq;                                  // rows below cut cannot reach the top k
+      int cnt = 0;
+      bool ovf = false;
+      // register mode (KMAX > 0): the k best screened scores in registers and
+      // up to kCand candidates in shared memory.  Heap mode (KMAX == 0): the
+      // k best screened scores in a shared-memory min-heap and up to kc
+      // candidates in the slot's global list.
+      float ta[KMAX > 0 ? KMAX : 1];
+#pragma unroll
+      for (int j = 0; j < (KMAX > 0 ? KMAX : 1); ++j) ta[j] = -INFINITY;
+      float* cub = ext_s + m;                                              // [kCand][kM] scores
+      int32_t* cpos = reinterpret_cast<int32_t*>(ext_s + kM * kCand) + m;   // [kCand][kM] padded rows
+      float* heap = ext_s + m;                                             // heap mode: [k][kM]
+      int hn = 0;
+      Cand* glist = P.cand + (e0 + (active ? jq : 0)) * (int64_t)P.kc;     // heap mode candidates
       for (int i = 0; i < ntiles; ++i) {
-        const uint32_t T = tile_ctr + i, s = T % S, b = T & 1, tph = (T >> 1) & 1;
+        const uint32_t T = tile_ctr + i, b = T & 1, tph = (T >> 1) & 1;
         const bool ok = tc::bar_wait(tfull(b), tph, abort_v);
         if (!ok) give_up();
         tc::fence_after_sync();
         uint32_t r0[32], r1[32];
         const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + b * kN;
-        tc::tmem_ld32(taddr, r0);
-        tc::tmem_ld32(taddr + 32, r1);
-        tc::tmem_ld_wait();
+        if (ok) {
+          tc::tmem_ld32(taddr, r0);
+          tc::tmem_ld32(taddr + 32, r1);
+          tc::tmem_ld_wait();
+        }
         tc::fence_before_sync();
         __syncwarp();
         if (lane == 0) tc::bar_arrive(tempty(b));
         if (!ok) break;
         const int nvalid = min(kN, nrows - kN * i);
         const int32_t pr0 = (int32_t)((g0 + 8 * i) * 8);
-        if (KMAX > 0 && ak == -INFINITY && k <= 16 && nvalid == kN) {
+        if (KMAX > 0 && ak == -INFINITY && floor_ == -INFINITY && k <= 16 && nvalid == kN) {
           // the k-th largest of 16 group maxima (groups of 4 rows) is a lower
           // bound of the tile's k-th best screened score: seed the cut with it
           float g[16];
@@ -280,21 +342,22 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
           cut = fmaxf(seed - 2.f * dlt, gq);
         }
         // register-only screen against the cut at the tile's start (the cut
-        // only rises, so this keeps a superset); scores parked in smem
+        // only rises, so this keeps a superset); survivors parked in smem
         uint64_t mask = 0;
 #pragma unroll
         for (int c = 0; c < kN; ++c) {
           const float a = __uint_as_float(c < 32 ? r0[c & 31] : r1[c & 31]);
-          av_s[c * kM + m] = a;
-          mask |= (uint64_t)(c < nvalid && a >= cut) << c;
+          if (active && c < nvalid && a >= cut) {
+            mask |= (uint64_t)1 << c;
+            av_s[c * kM + m] = a;
+          }
         }
-        if (!active) mask = 0;
         // pass 1: the tile's survivors raise the k best screened scores
         for (uint64_t m1 = mask; m1; m1 &= m1 - 1) {
           const int c = __ffsll((long long)m1) - 1;
           const float a = av_s[c * kM + m];
           if constexpr (KMAX > 0) {
-            if (a > ak && a >= cut) {
+            if (a > ak) {
               float v = a;
 #pragma unroll
               for (int j = 0; j < KMAX; ++j) {
@@ -373,8 +436,6 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
             else ovf = true;
           }
         }
-        __syncwarp();
-        if (lane == 0) tc::bar_arrive(empty(s));
       }
       if (active && !abort_s) {
         const int64_t e = e0 + jq;
@@ -404,9 +465,9 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
     volatile int never = 0;
     for (int T = consumed_s; T < issued_s; ++T) tc::bar_wait(full(T % S), (T / S) & 1, &never);
   }
-  if (abort_s && threadIdx.x == 32 && mma_issued_s > 0) {
+  if (abort_s && threadIdx.x == 64 && committed_s > 0) {
     volatile int never = 0;
-    const int T = mma_issued_s - 1;
+    const int T = committed_s - 1;
     tc::bar_wait(tfull(T & 1), (T >> 1) & 1, &never);
   }
   tc::fence_before_sync();
@@ -417,12 +478,12 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
 
 size_t smem_bytes(int kp, int k, int stages) {
   return 1024 + (size_t)kM * kp * 4 + (size_t)stages * kN * kp * 4 + (size_t)kN * kM * 4 + ext_bytes(k) +
-         (size_t)(2 * stages + 4) * 8;
+         (size_t)kM * 4 + (size_t)(2 * stages + 4) * 8;
 }
 
 int pick_stages(int kp, int k) {
   for (int s = kMaxStages; s >= 2; --s)
-    if (smem_bytes(kp, k, s) <= 227 * 1024) return s;
+    if (smem_bytes(kp, k, s) <= 227 * 1024 - 1024) return s;   // room for the static shared variables
   return 0;
 }
 

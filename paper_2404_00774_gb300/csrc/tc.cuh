@@ -103,6 +103,12 @@ __device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void* src, uin
       : "memory");
 }
 
+// Asynchronous prefetch of a contiguous global range into L2 (16-byte
+// aligned address, size a multiple of 16); nothing to wait for.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // 16-byte asynchronous global -> shared copy (both addresses 16-byte aligned),
 // completed by cp_async_wait_all in the issuing thread.
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
