@@ -190,19 +190,25 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
     const int ng = D.ng;
     const int ntiles = (ng + 7) / 8;
 
-    // ---- queries of the item -> A operand (row m of the epilogue threads)
+    // ---- queries of the item -> A operand (row m of the epilogue threads),
+    // staged by 16-byte cp.async so that the row's loads are all in flight
+    // at once; the producer warp is not held by this barrier and already
+    // streams the item's tiles
     if (warp >= 3) {
-      const bool active = jq < nqi;
-      const float* q = active ? P.Qf + P.work.query(e0 + jq) * (int64_t)kp : nullptr;
       float* arow = sA + (m >> 3) * (kp * 8) + (m & 7) * 4;
-      for (int k4 = 0; k4 < kp / 4; ++k4) {
-        float4 v = active ? *reinterpret_cast<const float4*>(q + 4 * k4) : make_float4(0.f, 0.f, 0.f, 0.f);
-        *reinterpret_cast<float4*>(arow + k4 * 32) = v;
+      if (jq < nqi) {
+        const int64_t qi = P.work.query(e0 + jq);
+        const float* q = P.Qf + qi * (int64_t)kp;
+        for (int k4 = 0; k4 < kp / 4; ++k4) tc::cp_async16(tc::smem_u32(arow + k4 * 32), q + 4 * k4);
+        qn_s[m] = P.qnorm[qi];
+      } else {
+        for (int k4 = 0; k4 < kp / 4; ++k4) *reinterpret_cast<float4*>(arow + k4 * 32) = make_float4(0.f, 0.f, 0.f, 0.f);
+        qn_s[m] = 0.f;
       }
-      qn_s[m] = active ? P.qnorm[P.work.query(e0 + jq)] : 0.f;
+      tc::cp_async_wait_all();
       tc::fence_async_smem();
     }
-    __syncthreads();
+    if (warp > 0) asm volatile("bar.sync 3, %0;" ::"n"(kThreads - 32) : "memory");
 
     if (warp == 0) {
       // ---- producer: one thread streams the partition's tiles, keeping the
