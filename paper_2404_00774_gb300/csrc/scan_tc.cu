@@ -107,13 +107,16 @@ __device__ ItemDesc describe_item(const TcParams& P, int item, int total) {
   return d;
 }
 
-template <int KMAX>
+// KMAX > 0: register top-k of up to KMAX entries (EXACT: k == KMAX known at
+// compile time, which makes every top-k insertion a fixed compare-exchange
+// chain); KMAX == 0: heap mode.
+template <int KMAX, bool EXACT>
 __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte aligned carve-up of the dynamic shared memory
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const int kp = P.kp, k = P.k, S = P.stages;
+  const int kp = P.kp, k = EXACT ? KMAX : P.k, S = P.stages;
   const uint32_t sbo = (uint32_t)kp * 32u;            // bytes between 8-row groups
   const uint32_t a_bytes = (uint32_t)kM * kp * 4u;
   const uint32_t b_bytes = (uint32_t)kN * kp * 4u;
@@ -771,7 +774,9 @@ void scan_tc_search(const IndexData& ix, const IvfWork& work, int max_items, con
   prm.counter = scr.get<int>(1);
   SOAR_CUDA(cudaMemsetAsync(prm.counter, 0, sizeof(int), s));
   const size_t smem = smem_bytes(ix.tc_kp, k, stages);
-  auto kern = k <= 16 ? scan_tc_kernel<16> : k <= kCand ? scan_tc_kernel<32> : scan_tc_kernel<0>;
+  auto kern = k == 10   ? scan_tc_kernel<10, true>
+              : k <= 16 ? scan_tc_kernel<16, false>
+              : k <= kCand ? scan_tc_kernel<32, false> : scan_tc_kernel<0, false>;
   SOAR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int grid = std::max(1, std::min(max_items, num_sms()));
   stage_mark(s, "scan", true);
