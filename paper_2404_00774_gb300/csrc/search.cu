@@ -333,6 +333,43 @@ __global__ void __launch_bounds__(256) topt_kernel(const float* __restrict__ S, 
   }
 }
 
+// Top-t for t <= 32, a warp per query: lane j holds the query's j-th best
+// (score, id) key so far (ascending rank keys: higher score first, lower id
+// on ties); the row streams through in coalesced chunks of 32, a ballot
+// keeps the chunk's keys that beat the current t-th, and each is inserted by
+// one ballot (its position) and one shuffle (the shift).
+__global__ void __launch_bounds__(256) topt_warp_kernel(const float* __restrict__ S, int64_t nq, int c, int t,
+                                                        int32_t* __restrict__ top, float* __restrict__ top_s) {
+  constexpr unsigned kFull = 0xffffffffu;
+  const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (q >= nq) return;
+  const float* row = S + q * c;
+  uint64_t mine = ~0ull;          // empty entries rank after every real key
+  uint64_t thr = ~0ull;           // the t-th best key
+  for (int c0 = 0; c0 < c; c0 += 32) {
+    const int i = c0 + lane;
+    const uint64_t key = i < c ? rank_key(row[i], (uint32_t)i) : ~0ull;
+    unsigned bal = __ballot_sync(kFull, key < thr);
+    while (bal) {
+      const int src = __ffs(bal) - 1;
+      bal &= bal - 1;
+      const uint64_t kk = __shfl_sync(kFull, key, src);
+      if (kk >= thr) continue;                       // the same in every lane
+      const int pos = __popc(__ballot_sync(kFull, lane < t && mine < kk));
+      const uint64_t up = __shfl_up_sync(kFull, mine, 1);
+      if (lane > pos && lane < t) mine = up;
+      if (lane == pos) mine = kk;
+      thr = __shfl_sync(kFull, mine, t - 1);
+    }
+  }
+  if (lane < t) {
+    const uint32_t id = (uint32_t)(mine & 0xffffffffu);
+    top[q * t + lane] = (int32_t)id;
+    if (top_s) top_s[q * t + lane] = row[id];
+  }
+}
+
 // ------------------------------------------------------------ grouping
 
 __global__ void make_pairs(const int32_t* __restrict__ top, int64_t nq, int tmax, const int32_t* __restrict__ tpq,
@@ -732,6 +769,11 @@ void select_prepared(const IndexData& ix, const float* Qf, const float* qscale, 
                      int32_t* top, float* top_s, cudaStream_t s, Scratch& scr) {
   float* S = scr.get<float>((size_t)nq * ix.c);
   score_centroids(ix, Qf, qscale, nq, qstride, S, s);
+  if (t <= 32) {
+    topt_warp_kernel<<<ceil_div(nq * 32, 256), 256, 0, s>>>(S, nq, ix.c, t, top, top_s);
+    SOAR_LAUNCHED();
+    return;
+  }
   const int t2 = pow2_at_least(t);
   const int smem = t2 * 8 + (ix.c <= kToptSmemRow ? ix.c * 4 : 0);
   SOAR_CUDA(cudaFuncSetAttribute(topt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
