@@ -51,12 +51,15 @@ struct IvfWork {
 
 // Tensor-core scan (scan_tc.cu) of a fp32 index (rows in the core-matrix
 // layout of tc.cuh, queries as fp32 rows of tc_kp columns): screening on the
-// tensor cores, then exact rescoring; leaves in `lists` one list of
-// scan_tc_list_len(k) (exact score, id) entries per pair slot, best first,
-// an id of -1 closing a shorter list.  k <= scan_tc_max_k(ix) (at most 128).
-void scan_tc_search(const IndexData& ix, const IvfWork& work, int max_items, const float* Qf, const float* qnorm,
+// tensor cores, then exact rescoring.  For k <= 32 it also merges: the
+// final top k of every query goes to ids_out / scores_out and it returns
+// true.  Otherwise it leaves in `lists` one list of scan_tc_list_len(k)
+// (exact score, id) entries per pair slot, best first, an id of -1 closing
+// a shorter list, for the caller's merge, and returns false.
+// k <= scan_tc_max_k(ix) (at most 128).
+bool scan_tc_search(const IndexData& ix, const IvfWork& work, int max_items, const float* Qf, const float* qnorm,
                     const int32_t* top, const int32_t* inv, const int32_t* tpq, int64_t nq, int t, int k,
-                    Cand* lists, int* err, cudaStream_t s, Scratch& scr);
+                    Cand* lists, int* err, int64_t* ids_out, float* scores_out, cudaStream_t s, Scratch& scr);
 int scan_tc_max_k(const IndexData& ix);
 int scan_tc_list_len(int k);
 

@@ -19,10 +19,11 @@
 //     below, and
 //   * the rows with s~ + delta >= L_k (up to kCand, pruned as a_k rises);
 //     a row outside that set cannot be in the top k.
-// No row is rescored here.  rescore_lists() later takes, per query, the
-// largest L_k over its partitions, rescores exactly the candidates whose
-// upper bound reaches it and rescans exactly any partition whose candidate
-// list overflowed, so the final lists equal those of an exact scan.
+// No row is rescored here.  finish_queries() (rescore_wide() and the merge
+// for k > 32) later takes, per query, the largest L_k over its partitions,
+// rescores exactly the candidates whose upper bound reaches it and rescans
+// exactly any partition whose candidate list overflowed, so the results
+// equal those of an exact scan.
 //
 // Warp roles: 0 = bulk-copy producer (it also claims and resolves the next
 // work item ahead and prefetches its first tiles into L2), 1 = TMEM owner and
@@ -514,8 +515,11 @@ __device__ __forceinline__ float exact_dot(const float* __restrict__ q, const fl
                                            int64_t pos) {
   const float* x = rows + (pos >> 3) * (int64_t)(8 * kp) + (pos & 7) * 4;
   float acc = 0.f;
+  // unrolled so that several row loads are in flight; the accumulation order
+  // (k ascending) is fixed, so both spilled copies of a point score the same
+#pragma unroll 8
   for (int k4 = 0; k4 < kp / 4; ++k4) {
-    const float4 a = *reinterpret_cast<const float4*>(q + 4 * k4);
+    const float4 a = __ldg(reinterpret_cast<const float4*>(q + 4 * k4));
     const float4 v = __ldg(reinterpret_cast<const float4*>(x + k4 * 32));
     acc = fmaf(a.x, v.x, acc);
     acc = fmaf(a.y, v.y, acc);
@@ -525,99 +529,9 @@ __device__ __forceinline__ float exact_dot(const float* __restrict__ q, const fl
   return acc;
 }
 
-// Warp per (query, partition) slot: the candidates whose upper bound reaches
-// the query's bound are rescored exactly; a slot whose list overflowed is
-// rescanned exactly over its whole partition (its exact top-k kept).  The
-// slot is rewritten as a list of (exact score, id), best first, padded with
-// (-inf, -1).
-__global__ void __launch_bounds__(256) rescore_lists(Cand* __restrict__ cand, const int2* __restrict__ hdr,
-                                                     int64_t P, const int32_t* __restrict__ pair_vals, int t,
-                                                     const float* __restrict__ lstar, const float* __restrict__ Qf,
-                                                     int kp, const float* __restrict__ rows,
-                                                     const int32_t* __restrict__ ids,
-                                                     const int32_t* __restrict__ part_of_pair,
-                                                     const int64_t* __restrict__ gstart,
-                                                     const int64_t* __restrict__ part_off, int k,
-                                                     const int32_t* __restrict__ tpq) {
-  const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (e >= P) return;
-  const int64_t q = pair_vals[e] / t;
-  const int j = pair_vals[e] - (int)(q * t);
-  if (tpq && j >= min(max(tpq[q], 1), t)) return;   // a probe beyond the query's own t: no list
-  const int2 h = hdr[e];
-  const int cnt = h.y & 0x7fffffff;
-  const bool ovf = h.y < 0;
-  const float bound = lstar[q];
-  const float* qv = Qf + q * (int64_t)kp;
-  Cand* slot = cand + e * kCand;
-  float s = -INFINITY;
-  int id = -1;
-  if (!ovf) {
-    if (lane < cnt) {
-      const Cand c = slot[lane];
-      if (c.s >= bound) {
-        s = exact_dot(qv, rows, kp, c.id);
-        id = ids[c.id];
-      }
-    }
-  } else {
-    // exact rescan of the partition; each lane keeps the best of its rows,
-    // then the warp keeps the k best overall (k <= 32)
-    const int p = part_of_pair[e];
-    const int64_t r0 = gstart[p] * 8;
-    const int64_t nrows = part_off[p + 1] - part_off[p];
-    Cand mine[kCand];
-    int have = 0;
-    for (int64_t r = lane; r < nrows; r += 32) {
-      const float v = exact_dot(qv, rows, kp, r0 + r);
-      const int rid = ids[r0 + r];
-      if (have < k || better(v, rid, mine[have - 1].s, mine[have - 1].id)) {
-        int pos = have < k ? have : k - 1;
-        while (pos > 0 && better(v, rid, mine[pos - 1].s, mine[pos - 1].id)) {
-          mine[pos] = mine[pos - 1];
-          --pos;
-        }
-        mine[pos] = Cand{v, rid};
-        if (have < k) ++have;
-      }
-    }
-    int head = 0;
-    for (int out = 0; out < k; ++out) {
-      float bs = head < have ? mine[head].s : -INFINITY;
-      int bid = head < have ? mine[head].id : -1;
-      int wl = head < have ? lane : 32;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const float os = __shfl_xor_sync(0xffffffffu, bs, o);
-        const int oid = __shfl_xor_sync(0xffffffffu, bid, o);
-        const int ol = __shfl_xor_sync(0xffffffffu, wl, o);
-        if (ol != 32 && (wl == 32 || better(os, oid, bs, bid))) { bs = os; bid = oid; wl = ol; }
-      }
-      if (lane == out) { s = bs; id = wl == 32 ? -1 : bid; }
-      if (wl != 32 && lane == wl) ++head;
-    }
-  }
-  // bitonic sort of the 32 lane values, best first
-#pragma unroll
-  for (int size = 2; size <= 32; size <<= 1) {
-#pragma unroll
-    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      const float os = __shfl_xor_sync(0xffffffffu, s, stride);
-      const int oid = __shfl_xor_sync(0xffffffffu, id, stride);
-      const bool up = (lane & size) == 0;          // this 'size' block sorts best-first
-      const bool lower = (lane & stride) == 0;
-      const bool other_better = better(os, oid, s, id);
-      const bool take = (lower == up) ? other_better : (!other_better && !(os == s && oid == id));
-      if (take) { s = os; id = oid; }
-    }
-  }
-  slot[lane] = Cand{s, id};
-}
-
-// Heap-mode counterpart of rescore_lists (32 < k <= 128, lists of kc <= 256
-// entries), a warp per (query, partition) slot: the candidates whose upper
-// bound reaches the query's bound are rescored exactly and the best k kept;
+// Rescoring for 32 < k <= 128 (heap mode, lists of kc <= 256 entries), a
+// warp per (query, partition) slot: the candidates whose upper bound reaches
+// the query's bound are rescored exactly and the best k kept;
 // a slot whose list overflowed is rescanned exactly over its partition into
 // a shared-memory top-k list.  The slot is rewritten best first and closed
 // by a (-inf, -1) entry when shorter than kc.
@@ -736,6 +650,110 @@ __global__ void __launch_bounds__(256) rescore_wide(Cand* __restrict__ cand, con
   if (lane == 0 && k < kc) slot[k] = Cand{-INFINITY, -1};
 }
 
+// Finishing pass for k <= 32, a warp per query: the query's bound L* (the
+// largest L_k of its partitions) bounds its final k-th best exact score from
+// below; every candidate whose upper bound reaches L* (and beats the current
+// k-th best) is rescored exactly, and every partition whose list overflowed
+// is rescanned exactly.  The exact results go into a lane-distributed sorted
+// top-k (lane j: j-th best rank key), dropping the second copy of a spilled
+// point (its exact score is bit-identical, so its key is too).  Writes the
+// query's ids / scores, padded with -1 / -inf.
+__global__ void __launch_bounds__(256) finish_queries(
+    const Cand* __restrict__ cand, const int2* __restrict__ hdr, const int32_t* __restrict__ inv, int64_t nq, int t,
+    const int32_t* __restrict__ tpq, const float* __restrict__ Qf, int kp, const float* __restrict__ rows,
+    const int32_t* __restrict__ ids, const int32_t* __restrict__ top, const int64_t* __restrict__ gstart,
+    const int64_t* __restrict__ part_off, int k, int kc, int64_t* __restrict__ ids_out,
+    float* __restrict__ scores_out) {
+  constexpr unsigned kFull = 0xffffffffu;
+  constexpr int kPend = 256;                    // pending candidates per warp
+  __shared__ int32_t pend_s[8][kPend];
+  const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (q >= nq) return;
+  const int tq = tpq ? min(max(tpq[q], 1), t) : t;
+  float lstar = -INFINITY;
+  for (int j = lane; j < tq; j += 32) lstar = fmaxf(lstar, __int_as_float(hdr[inv[q * t + j]].x));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) lstar = fmaxf(lstar, __shfl_xor_sync(kFull, lstar, o));
+  const float* qv = Qf + q * (int64_t)kp;
+  uint64_t mine = ~0ull;          // lane j < k: the j-th best key so far (empty: after every real key)
+  uint64_t thr = ~0ull;           // the k-th best key
+  // inserts the keys of this round (one per lane, ~0 for none)
+  auto insert_round = [&](uint64_t key) {
+    unsigned bal = __ballot_sync(kFull, key < thr);
+    while (bal) {
+      const int src = __ffs(bal) - 1;
+      bal &= bal - 1;
+      const uint64_t kk = __shfl_sync(kFull, key, src);
+      if (kk >= thr) continue;                                   // the same in every lane
+      if (__ballot_sync(kFull, lane < k && mine == kk)) continue;  // spilled copy already in
+      const int pos = __popc(__ballot_sync(kFull, lane < k && mine < kk));
+      const uint64_t up = __shfl_up_sync(kFull, mine, 1);
+      if (lane > pos && lane < k) mine = up;
+      if (lane == pos) mine = kk;
+      thr = __shfl_sync(kFull, mine, k - 1);
+    }
+  };
+  // candidates whose upper bound reaches L*, gathered over all of the
+  // query's partitions (padded row positions), then rescored 32 at a time so
+  // that the exact dot products of a round overlap
+  int32_t* pend = pend_s[threadIdx.x >> 5];
+  int npend = 0;
+  auto flush = [&]() {
+    for (int b = 0; b < npend; b += 32) {
+      const float kth = thr == ~0ull ? -INFINITY : key_float(~(uint32_t)(thr >> 32));
+      uint64_t key = ~0ull;
+      if (b + lane < npend) {
+        const int32_t pos = pend[b + lane];
+        const float v = exact_dot(qv, rows, kp, pos);
+        if (v >= kth) key = rank_key(v, (uint32_t)ids[pos]);
+      }
+      insert_round(key);
+    }
+    npend = 0;
+    __syncwarp();
+  };
+  int64_t e_l = 0;                // lane j % 32: slot and header of the query's probe j (32 at a time)
+  int2 h_l = make_int2(0, 0);
+  for (int j = 0; j < tq; ++j) {
+    if ((j & 31) == 0) {
+      if (j + lane < tq) {
+        e_l = inv[q * t + j + lane];
+        h_l = hdr[e_l];
+      }
+    }
+    const int64_t e = __shfl_sync(kFull, e_l, j & 31);
+    const int2 h = make_int2(__shfl_sync(kFull, h_l.x, j & 31), __shfl_sync(kFull, h_l.y, j & 31));
+    const int cnt = h.y & 0x7fffffff;
+    if (h.y >= 0) {
+      const Cand c = lane < cnt ? cand[e * kc + lane] : Cand{-INFINITY, 0};
+      const bool keep = lane < cnt && c.s >= lstar;
+      const unsigned kb = __ballot_sync(kFull, keep);
+      if (npend + __popc(kb) > kPend) flush();
+      if (keep) pend[npend + __popc(kb & ((1u << lane) - 1u))] = c.id;
+      npend += __popc(kb);
+      __syncwarp();
+    } else {
+      // the list overflowed: rescan the partition exactly
+      flush();
+      const int p = top[q * t + j];
+      const int64_t r0 = gstart[p] * 8;
+      const int64_t nrows = part_off[p + 1] - part_off[p];
+      for (int64_t base = 0; base < nrows; base += 32) {
+        const int64_t r = base + lane;
+        const uint64_t key = r < nrows ? rank_key(exact_dot(qv, rows, kp, r0 + r), (uint32_t)ids[r0 + r]) : ~0ull;
+        insert_round(key);
+      }
+    }
+  }
+  flush();
+  if (lane < k) {
+    const bool have = mine != ~0ull;
+    ids_out[q * k + lane] = have ? (int64_t)(uint32_t)(mine & 0xffffffffu) : -1;
+    scores_out[q * k + lane] = have ? key_float(~(uint32_t)(mine >> 32)) : -INFINITY;
+  }
+}
+
 __global__ void fill_u32(unsigned* __restrict__ a, int64_t n, unsigned v) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) a[i] = v;
@@ -758,9 +776,9 @@ int scan_tc_max_k(const IndexData& ix) {
 
 int scan_tc_list_len(int k) { return list_len_for(k); }
 
-void scan_tc_search(const IndexData& ix, const IvfWork& work, int max_items, const float* Qf, const float* qnorm,
+bool scan_tc_search(const IndexData& ix, const IvfWork& work, int max_items, const float* Qf, const float* qnorm,
                     const int32_t* top, const int32_t* inv, const int32_t* tpq, int64_t nq, int t, int k,
-                    Cand* lists, int* err, cudaStream_t s, Scratch& scr) {
+                    Cand* lists, int* err, int64_t* ids_out, float* scores_out, cudaStream_t s, Scratch& scr) {
   const int stages = pick_stages(ix.tc_kp, k);
   if (stages < 2 || k > kWideK) fail(SOAR_EUNSUPPORTED, "tensor-core scan: k too large");
   const int kc = list_len_for(k);
@@ -784,22 +802,26 @@ void scan_tc_search(const IndexData& ix, const IvfWork& work, int max_items, con
   SOAR_LAUNCHED();
   stage_mark(s, "scan", false);
   stage_mark(s, "rescore", true);
+  if (k <= kCand) {
+    finish_queries<<<ceil_div(nq * 32, 256), 256, 0, s>>>(lists, hdr, inv, nq, t, tpq, Qf, ix.tc_kp, ix.tc_rows,
+                                                          ix.tc_ids, top, ix.tc_gstart, ix.offsets, k, kc, ids_out,
+                                                          scores_out);
+    SOAR_LAUNCHED();
+    stage_mark(s, "rescore", false);
+    return true;
+  }
   float* lstar = scr.get<float>(nq);
   query_bounds<<<ceil_div(nq, 256), 256, 0, s>>>(hdr, inv, nq, t, tpq, lstar);
   SOAR_LAUNCHED();
   int32_t* part = scr.get<int32_t>(P);
   pair_partitions<<<ceil_div(P, 256), 256, 0, s>>>(top, work.pair_vals, P, part);
   SOAR_LAUNCHED();
-  if (k <= kCand)
-    rescore_lists<<<ceil_div(P * 32, 256), 256, 0, s>>>(lists, hdr, P, work.pair_vals, t, lstar, Qf, ix.tc_kp,
-                                                        ix.tc_rows, ix.tc_ids, part, ix.tc_gstart, ix.offsets, k,
-                                                        tpq);
-  else
-    rescore_wide<<<ceil_div(P * 32, 256), 256, 0, s>>>(lists, hdr, P, work.pair_vals, t, lstar, Qf, ix.tc_kp,
-                                                       ix.tc_rows, ix.tc_ids, part, ix.tc_gstart, ix.offsets, k, kc,
-                                                       tpq);
+  rescore_wide<<<ceil_div(P * 32, 256), 256, 0, s>>>(lists, hdr, P, work.pair_vals, t, lstar, Qf, ix.tc_kp,
+                                                     ix.tc_rows, ix.tc_ids, part, ix.tc_gstart, ix.offsets, k, kc,
+                                                     tpq);
   SOAR_LAUNCHED();
   stage_mark(s, "rescore", false);
+  return false;
 }
 
 }  // namespace soar

@@ -917,7 +917,9 @@ void search(const IndexData& ix, const void* Q, soar_dtype dt, int64_t nq, int32
     Cand* lists = scr.get<Cand>((size_t)P * len);
     Grouped g = group_pairs(ix, nq, t, tpq, 128, top, inv, s, scr);
     IvfWork work{ix.offsets, g.pair_off, g.vals, ix.part_order, g.item_base, ix.c, t, 128};
-    scan_tc_search(ix, work, g.max_items, Qf, qn, top, inv, tpq, nq, t, k, lists, device_error_word(), s, scr);
+    if (scan_tc_search(ix, work, g.max_items, Qf, qn, top, inv, tpq, nq, t, k, lists, device_error_word(), ids_out,
+                       scores_out, s, scr))
+      return;                                   // rescored and merged by the scan's finishing kernel
     const int smem = 4 * t * (int)sizeof(uint16_t);
     SOAR_CUDA(cudaFuncSetAttribute(merge_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     stage_mark(s, "merge", true);
