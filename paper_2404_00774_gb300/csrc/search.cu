@@ -372,21 +372,32 @@ __global__ void __launch_bounds__(256) topt_warp_kernel(const float* __restrict_
 
 // ------------------------------------------------------------ grouping
 
-__global__ void make_pairs(const int32_t* __restrict__ top, int64_t nq, int tmax, const int32_t* __restrict__ tpq,
-                           int c, uint32_t* __restrict__ keys, int32_t* __restrict__ vals) {
-  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// Counting sort of the (query, probe) pairs by partition: per-partition
+// counts (a probe beyond the query's own t counts in the sentinel bucket c),
+// then a scatter that also records each pair's position (the inverse map).
+// The order of the pairs inside a partition is immaterial to the search.
+__global__ void pair_counts(const int32_t* __restrict__ top, int64_t nq, int tmax, const int32_t* __restrict__ tpq,
+                            int c, unsigned long long* __restrict__ cnt) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nq * tmax) return;
-  int64_t q = e / tmax;
-  int j = (int)(e - q * tmax);
-  int tq = tmax;
-  if (tpq) tq = min(max(tpq[q], 1), tmax);
-  keys[e] = j < tq ? (uint32_t)top[e] : (uint32_t)c;
-  vals[e] = (int32_t)e;
+  const int64_t q = e / tmax;
+  const int j = (int)(e - q * tmax);
+  const int tq = tpq ? min(max(tpq[q], 1), tmax) : tmax;
+  atomicAdd(&cnt[j < tq ? top[e] : c], 1ull);
 }
 
-__global__ void invert_pairs(const int32_t* __restrict__ vals_sorted, int64_t P, int32_t* __restrict__ inv) {
-  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < P) inv[vals_sorted[e]] = (int32_t)e;
+__global__ void pair_scatter(const int32_t* __restrict__ top, int64_t nq, int tmax, const int32_t* __restrict__ tpq,
+                             int c, const int64_t* __restrict__ pair_off, int32_t* __restrict__ cursor,
+                             int32_t* __restrict__ vals, int32_t* __restrict__ inv) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nq * tmax) return;
+  const int64_t q = e / tmax;
+  const int j = (int)(e - q * tmax);
+  const int tq = tpq ? min(max(tpq[q], 1), tmax) : tmax;
+  const int b = j < tq ? top[e] : c;
+  const int64_t pos = pair_off[b] + atomicAdd(&cursor[b], 1);
+  vals[pos] = (int32_t)e;
+  inv[e] = (int32_t)pos;
 }
 
 __global__ void item_counts(const int64_t* __restrict__ pair_off, const int32_t* __restrict__ order, int c,
@@ -788,34 +799,33 @@ struct Grouped {
   int max_items;
 };
 
-// (query, probe) pairs sorted by partition with a stable radix sort, the
-// inverse map inv[q * t + j] = sorted position, and the work items
-// (partition, <= qb pairs) counted over partitions in size order.
+// (query, probe) pairs grouped by partition (counting sort), the inverse
+// map inv[q * t + j] = grouped position, and the work items (partition,
+// <= qb pairs) counted over partitions in size order.
 Grouped group_pairs(const IndexData& ix, int64_t nq, int t, const int32_t* tpq, int qb, const int32_t* top,
                     int32_t* inv, cudaStream_t s, Scratch& scr) {
   const int64_t P = nq * t;
-  uint32_t* keys = scr.get<uint32_t>(P);
-  int32_t* vals = scr.get<int32_t>(P);
-  uint32_t* keys2 = scr.get<uint32_t>(P);
-  int32_t* vals2 = scr.get<int32_t>(P);
+  const int c = ix.c;
   stage_mark(s, "group", true);
-  make_pairs<<<ceil_div(P, 256), 256, 0, s>>>(top, nq, t, tpq, ix.c, keys, vals);
+  unsigned long long* cnt = scr.get<unsigned long long>((size_t)c + 2);
+  int32_t* cursor = scr.get<int32_t>((size_t)c + 1);
+  SOAR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * (c + 2), s));
+  SOAR_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int32_t) * (c + 1), s));
+  pair_counts<<<ceil_div(P, 256), 256, 0, s>>>(top, nq, t, tpq, c, cnt);
   SOAR_LAUNCHED();
-  bool in_tmp = radix_sort_pairs(keys, vals, keys2, vals2, P, bits_for((int64_t)ix.c + 1), s, scr);
-  const uint32_t* ks = in_tmp ? keys2 : keys;
-  const int32_t* vs = in_tmp ? vals2 : vals;
   Grouped g;
-  g.pair_off = scr.get<int64_t>((size_t)ix.c + 1);
-  segment_offsets(ks, P, ix.c, g.pair_off, s);
-  invert_pairs<<<ceil_div(P, 256), 256, 0, s>>>(vs, P, inv);
+  g.pair_off = scr.get<int64_t>((size_t)c + 2);
+  exclusive_scan_i64(reinterpret_cast<const int64_t*>(cnt), g.pair_off, (int64_t)c + 2, s, scr);
+  int32_t* vals = scr.get<int32_t>(P);
+  pair_scatter<<<ceil_div(P, 256), 256, 0, s>>>(top, nq, t, tpq, c, g.pair_off, cursor, vals, inv);
   SOAR_LAUNCHED();
-  g.item_base = scr.get<int32_t>((size_t)ix.c + 1);
-  item_counts<<<ceil_div((int64_t)ix.c + 1, 256), 256, 0, s>>>(g.pair_off, ix.part_order, ix.c, qb, g.item_base);
+  g.item_base = scr.get<int32_t>((size_t)c + 1);
+  item_counts<<<ceil_div((int64_t)c + 1, 256), 256, 0, s>>>(g.pair_off, ix.part_order, c, qb, g.item_base);
   SOAR_LAUNCHED();
-  exclusive_scan_i32(g.item_base, g.item_base, (int64_t)ix.c + 1, s, scr);
+  exclusive_scan_i32(g.item_base, g.item_base, (int64_t)c + 1, s, scr);
   stage_mark(s, "group", false);
-  g.vals = vs;
-  g.max_items = (int)std::min<int64_t>(P / qb + ix.c + 1, 1 << 30);
+  g.vals = vals;
+  g.max_items = (int)std::min<int64_t>(P / qb + c + 1, 1 << 30);
   return g;
 }
 
