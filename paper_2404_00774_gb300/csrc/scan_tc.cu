@@ -74,7 +74,7 @@ struct TcParams {
   int* counter;            // work-item counter
   int* err;                // set to 1 when a wait expired
   unsigned* gbound;        // [nq] per-query lower bound of the final k-th best exact score (ordered key)
-  Cand* cand;              // [pairs][kc] (ub, padded row) candidates
+  Cand* cand;              // [pairs][kc] (ub, row-major row position) candidates
   int2* hdr;               // [pairs] (L_k as float bits, count | overflow << 31)
 };
 
@@ -90,7 +90,7 @@ __device__ __forceinline__ float unordered(unsigned k) {
 // and query count, its row count, first 8-row group and group count.
 struct ItemDesc {
   int p, nqi, nrows, ng;
-  int64_t e0, g0;
+  int64_t e0, g0, row0;
 };
 
 __device__ ItemDesc describe_item(const TcParams& P, int item, int total) {
@@ -102,7 +102,8 @@ __device__ ItemDesc describe_item(const TcParams& P, int item, int total) {
   d.p = p;
   d.e0 = P.work.pair_off[p] + (int64_t)(item - P.work.item_base[oi]) * kM;
   d.nqi = (int)min((int64_t)kM, P.work.pair_off[p + 1] - d.e0);
-  d.nrows = (int)(P.work.part_off[p + 1] - P.work.part_off[p]);
+  d.row0 = P.work.part_off[p];
+  d.nrows = (int)(P.work.part_off[p + 1] - d.row0);
   d.g0 = P.gstart[p];
   d.ng = (int)(P.gstart[p + 1] - d.g0);
   return d;
@@ -315,7 +316,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
         if (lane == 0) tc::bar_arrive(tempty(b));
         if (!ok) break;
         const int nvalid = min(kN, nrows - kN * i);
-        const int32_t pr0 = (int32_t)((g0 + 8 * i) * 8);
+        const int32_t pr0 = (int32_t)(D.row0 + (int64_t)kN * i);   // row-major position of the tile's first row
         if (KMAX > 0 && ak == -INFINITY && floor_ == -INFINITY && k <= 16 && nvalid == kN) {
           // the k-th largest of 16 group maxima (groups of 4 rows) is a lower
           // bound of the tile's k-th best screened score: seed the cut with it
@@ -510,17 +511,16 @@ __global__ void query_bounds(const int2* __restrict__ hdr, const int32_t* __rest
   lstar[q] = best;
 }
 
-// Exact fp32 <q, x> of padded row `pos` (k ascending, one thread).
-__device__ __forceinline__ float exact_dot(const float* __restrict__ q, const float* __restrict__ rows, int kp,
-                                           int64_t pos) {
-  const float* x = rows + (pos >> 3) * (int64_t)(8 * kp) + (pos & 7) * 4;
+// Exact fp32 <q, x> of row-major row `pos` (row stride rs, a multiple of 4;
+// k ascending, the same order for every copy of a point).
+__device__ __forceinline__ float exact_dot_rm(const float* __restrict__ q, const float* __restrict__ vec, int rs,
+                                              int64_t pos) {
+  const float* x = vec + pos * (int64_t)rs;
   float acc = 0.f;
-  // unrolled so that several row loads are in flight; the accumulation order
-  // (k ascending) is fixed, so both spilled copies of a point score the same
 #pragma unroll 8
-  for (int k4 = 0; k4 < kp / 4; ++k4) {
+  for (int k4 = 0; k4 < rs / 4; ++k4) {
     const float4 a = __ldg(reinterpret_cast<const float4*>(q + 4 * k4));
-    const float4 v = __ldg(reinterpret_cast<const float4*>(x + k4 * 32));
+    const float4 v = __ldg(reinterpret_cast<const float4*>(x + 4 * k4));
     acc = fmaf(a.x, v.x, acc);
     acc = fmaf(a.y, v.y, acc);
     acc = fmaf(a.z, v.z, acc);
@@ -528,6 +528,7 @@ __device__ __forceinline__ float exact_dot(const float* __restrict__ q, const fl
   }
   return acc;
 }
+
 
 // Rescoring for 32 < k <= 128 (heap mode, lists of kc <= 256 entries), a
 // warp per (query, partition) slot: the candidates whose upper bound reaches
@@ -538,7 +539,7 @@ __device__ __forceinline__ float exact_dot(const float* __restrict__ q, const fl
 __global__ void __launch_bounds__(256) rescore_wide(Cand* __restrict__ cand, const int2* __restrict__ hdr, int64_t P,
                                                     const int32_t* __restrict__ pair_vals, int t,
                                                     const float* __restrict__ lstar, const float* __restrict__ Qf,
-                                                    int kp, const float* __restrict__ rows,
+                                                    int kp, const float* __restrict__ rows, int rs,
                                                     const int32_t* __restrict__ ids,
                                                     const int32_t* __restrict__ part_of_pair,
                                                     const int64_t* __restrict__ gstart,
@@ -571,7 +572,7 @@ __global__ void __launch_bounds__(256) rescore_wide(Cand* __restrict__ cand, con
       if (idx < cnt) {
         const Cand c = slot[idx];
         if (c.s >= bound) {
-          v[r] = exact_dot(qv, rows, kp, c.id);
+          v[r] = exact_dot_rm(qv, rows, rs, c.id);
           id[r] = ids[c.id];
         }
       }
@@ -609,14 +610,14 @@ __global__ void __launch_bounds__(256) rescore_wide(Cand* __restrict__ cand, con
   for (int i = lane; i < k; i += 32) L[i] = Cand{-INFINITY, -1};
   __syncwarp();
   const int p = part_of_pair[e];
-  const int64_t r0 = gstart[p] * 8;
+  const int64_t r0 = part_off[p];
   const int64_t nrows = part_off[p + 1] - part_off[p];
   for (int64_t base = 0; base < nrows; base += 32) {
     const int64_t r = base + lane;
     float v = -INFINITY;
     int rid = -1;
     if (r < nrows) {
-      v = exact_dot(qv, rows, kp, r0 + r);
+      v = exact_dot_rm(qv, rows, rs, r0 + r);
       rid = ids[r0 + r];
     }
     unsigned ball = __ballot_sync(kFull, r < nrows && better(v, rid, L[k - 1].s, L[k - 1].id));
@@ -660,7 +661,7 @@ __global__ void __launch_bounds__(256) rescore_wide(Cand* __restrict__ cand, con
 // query's ids / scores, padded with -1 / -inf.
 __global__ void __launch_bounds__(256) finish_queries(
     const Cand* __restrict__ cand, const int2* __restrict__ hdr, const int32_t* __restrict__ inv, int64_t nq, int t,
-    const int32_t* __restrict__ tpq, const float* __restrict__ Qf, int kp, const float* __restrict__ rows,
+    const int32_t* __restrict__ tpq, const float* __restrict__ Qf, int kp, const float* __restrict__ rows, int rs,
     const int32_t* __restrict__ ids, const int32_t* __restrict__ top, const int64_t* __restrict__ gstart,
     const int64_t* __restrict__ part_off, int k, int kc, int64_t* __restrict__ ids_out,
     float* __restrict__ scores_out) {
@@ -705,7 +706,7 @@ __global__ void __launch_bounds__(256) finish_queries(
       uint64_t key = ~0ull;
       if (b + lane < npend) {
         const int32_t pos = pend[b + lane];
-        const float v = exact_dot(qv, rows, kp, pos);
+        const float v = exact_dot_rm(qv, rows, rs, pos);
         if (v >= kth) key = rank_key(v, (uint32_t)ids[pos]);
       }
       insert_round(key);
@@ -713,35 +714,61 @@ __global__ void __launch_bounds__(256) finish_queries(
     npend = 0;
     __syncwarp();
   };
-  int64_t e_l = 0;                // lane j % 32: slot and header of the query's probe j (32 at a time)
-  int2 h_l = make_int2(0, 0);
-  for (int j = 0; j < tq; ++j) {
-    if ((j & 31) == 0) {
-      if (j + lane < tq) {
-        e_l = inv[q * t + j + lane];
-        h_l = hdr[e_l];
-      }
+  // the query's probes 32 at a time: lane l holds probe j0 + l's slot and
+  // list length; a warp prefix sum over the lengths lets every lane load one
+  // candidate of any of the 32 lists in the same round
+  for (int j0 = 0; j0 < tq; j0 += 32) {
+    const int j = j0 + lane;
+    int64_t e_l = 0;
+    int cnt_l = 0;
+    bool ovf_l = false;
+    if (j < tq) {
+      e_l = inv[q * t + j];
+      const int hy = hdr[e_l].y;
+      ovf_l = hy < 0;
+      cnt_l = ovf_l ? 0 : (hy & 0x7fffffff);
     }
-    const int64_t e = __shfl_sync(kFull, e_l, j & 31);
-    const int2 h = make_int2(__shfl_sync(kFull, h_l.x, j & 31), __shfl_sync(kFull, h_l.y, j & 31));
-    const int cnt = h.y & 0x7fffffff;
-    if (h.y >= 0) {
-      const Cand c = lane < cnt ? cand[e * kc + lane] : Cand{-INFINITY, 0};
-      const bool keep = lane < cnt && c.s >= lstar;
+    int incl = cnt_l;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const int total = __shfl_sync(kFull, incl, 31);
+    for (int base = 0; base < total; base += 32) {
+      const int f = base + lane;
+      // the list holding entry f: the first lane whose inclusive sum exceeds f
+      int lo = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const int probe = __shfl_sync(kFull, incl, lo + step - 1);
+        if (probe <= f) lo += step;
+      }
+      const int64_t e = __shfl_sync(kFull, e_l, lo);
+      const int first = __shfl_sync(kFull, incl, lo) - __shfl_sync(kFull, cnt_l, lo);
+      bool keep = false;
+      int32_t pos = 0;
+      if (f < total) {
+        const Cand c = cand[e * kc + (f - first)];
+        keep = c.s >= lstar;
+        pos = c.id;
+      }
       const unsigned kb = __ballot_sync(kFull, keep);
       if (npend + __popc(kb) > kPend) flush();
-      if (keep) pend[npend + __popc(kb & ((1u << lane) - 1u))] = c.id;
+      if (keep) pend[npend + __popc(kb & ((1u << lane) - 1u))] = pos;
       npend += __popc(kb);
       __syncwarp();
-    } else {
-      // the list overflowed: rescan the partition exactly
+    }
+    // lists that overflowed: rescan their partitions exactly
+    for (unsigned ob = __ballot_sync(kFull, ovf_l); ob; ob &= ob - 1) {
+      const int l = __ffs(ob) - 1;
       flush();
-      const int p = top[q * t + j];
-      const int64_t r0 = gstart[p] * 8;
+      const int p = top[q * t + j0 + l];
+      const int64_t r0 = part_off[p];
       const int64_t nrows = part_off[p + 1] - part_off[p];
-      for (int64_t base = 0; base < nrows; base += 32) {
-        const int64_t r = base + lane;
-        const uint64_t key = r < nrows ? rank_key(exact_dot(qv, rows, kp, r0 + r), (uint32_t)ids[r0 + r]) : ~0ull;
+      for (int64_t rb = 0; rb < nrows; rb += 32) {
+        const int64_t r = rb + lane;
+        const uint64_t key = r < nrows ? rank_key(exact_dot_rm(qv, rows, rs, r0 + r), (uint32_t)ids[r0 + r]) : ~0ull;
         insert_round(key);
       }
     }
@@ -803,8 +830,9 @@ bool scan_tc_search(const IndexData& ix, const IvfWork& work, int max_items, con
   stage_mark(s, "scan", false);
   stage_mark(s, "rescore", true);
   if (k <= kCand) {
-    finish_queries<<<ceil_div(nq * 32, 256), 256, 0, s>>>(lists, hdr, inv, nq, t, tpq, Qf, ix.tc_kp, ix.tc_rows,
-                                                          ix.tc_ids, top, ix.tc_gstart, ix.offsets, k, kc, ids_out,
+    finish_queries<<<ceil_div(nq * 32, 256), 256, 0, s>>>(lists, hdr, inv, nq, t, tpq, Qf, ix.tc_kp,
+                                                          static_cast<const float*>(ix.vectors), ix.row_stride,
+                                                          ix.ids, top, ix.tc_gstart, ix.offsets, k, kc, ids_out,
                                                           scores_out);
     SOAR_LAUNCHED();
     stage_mark(s, "rescore", false);
@@ -817,8 +845,8 @@ bool scan_tc_search(const IndexData& ix, const IvfWork& work, int max_items, con
   pair_partitions<<<ceil_div(P, 256), 256, 0, s>>>(top, work.pair_vals, P, part);
   SOAR_LAUNCHED();
   rescore_wide<<<ceil_div(P * 32, 256), 256, 0, s>>>(lists, hdr, P, work.pair_vals, t, lstar, Qf, ix.tc_kp,
-                                                     ix.tc_rows, ix.tc_ids, part, ix.tc_gstart, ix.offsets, k, kc,
-                                                     tpq);
+                                                     static_cast<const float*>(ix.vectors), ix.row_stride, ix.ids,
+                                                     part, ix.tc_gstart, ix.offsets, k, kc, tpq);
   SOAR_LAUNCHED();
   stage_mark(s, "rescore", false);
   return false;
