@@ -315,6 +315,10 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
         __syncwarp();
         if (lane == 0) tc::bar_arrive(tempty(b));
         if (!ok) break;
+        // every fourth tile refresh G_q; the load is issued here and used
+        // after the tile's screening, so its latency overlaps that work
+        const bool refresh = active && (i & 3) == 3;
+        const unsigned gload = refresh ? __ldcg(P.gbound + qid) : 0u;
         const int nvalid = min(kN, nrows - kN * i);
         const int32_t pr0 = (int32_t)(D.row0 + (int64_t)kN * i);   // row-major position of the tile's first row
         if (KMAX > 0 && ak == -INFINITY && floor_ == -INFINITY && k <= 16 && nvalid == kN) {
@@ -413,7 +417,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
             }
           }
         }
-        if (active && (i & 3) == 3) gq = fmaxf(gq, unordered(__ldcg(P.gbound + qid)) - dlt);
+        if (refresh) gq = fmaxf(gq, unordered(gload) - dlt);
         cut = fmaxf(fmaxf(ak, floor_) - 2.f * dlt, gq);   // s~ + dlt < max(L_k, G_q)  <=>  s~ < cut
         // pass 2: keep the rows that survive the tile's final cut
         for (; mask; mask &= mask - 1) {
