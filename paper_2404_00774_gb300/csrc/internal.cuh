@@ -72,6 +72,11 @@ struct IndexData {
   int32_t tc_kp = 0;
   int64_t tc_groups = 0;
   int32_t* assign = nullptr;      // [n][1 + spills] copy of the assignment
+  // codebook packed for the tensor-core partition selection (select_tc.cu):
+  // tiles of 64 centroids, each the tf32 hi part then the lo part in the
+  // core-matrix layout (K = sel_kp); null when that kernel does not apply
+  float* sel_cb = nullptr;
+  int32_t sel_kp = 0, sel_tiles = 0;
 };
 
 }  // namespace soar
@@ -89,6 +94,20 @@ void free_index(IndexData& ix);
 
 void quantize_fp8(const void* V, soar_dtype dt, int64_t m, int32_t d, uint8_t* codes,
                   int32_t code_stride, float* scales, cudaStream_t s);
+
+// ----------------------------------------------------------- select_tc.cu
+
+// Whether the packed selection codebook of K = kp columns fits the kernel.
+bool select_tc_fits(int kp);
+// Fills out [sel_tiles][2][64 * sel_kp] from ix.centroids.
+void pack_select_codebook(const IndexData& ix, float* out, cudaStream_t s);
+// Whether select_tc takes these queries (packed codebook present, t <= 32,
+// rows 16-byte aligned).
+bool select_tc_usable(const IndexData& ix, const float* Qf, int qstride, int t);
+// top [nq][t] (and top_s, if not null): each query's t best centroids by
+// inner product, best first, lower id on ties; fp32 queries Qf [nq][qstride].
+void select_tc(const IndexData& ix, const float* Qf, int64_t nq, int qstride, int t, int32_t* top, float* top_s,
+               cudaStream_t s);
 
 // ----------------------------------------------------------- search.cu
 

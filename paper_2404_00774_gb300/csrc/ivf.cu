@@ -278,13 +278,20 @@ void build_index(IndexData& ix, const void* X, soar_dtype dt, const float* C, co
     partition_max_norm<<<c, 256, 0, s>>>(ix.tc_norms, ix.tc_gstart, ix.tc_pmax);
     SOAR_LAUNCHED();
   }
+  // fp32 centroid scores: the codebook packed for the tensor-core selection
+  if (ix.mode != SOAR_SCORE_FP8 && select_tc_fits((d + 7) / 8 * 8)) {
+    ix.sel_kp = (d + 7) / 8 * 8;
+    ix.sel_tiles = (c + 63) / 64;
+    dev_alloc((void**)&ix.sel_cb, sizeof(float) * 2 * 64 * (size_t)ix.sel_kp * ix.sel_tiles);
+    pack_select_codebook(ix, ix.sel_cb, s);
+  }
   SOAR_CUDA(cudaStreamSynchronize(s));
 }
 
 void free_index(IndexData& ix) {
   void* ptrs[] = {ix.offsets, ix.ids, ix.vectors, ix.row_scales, ix.originals, ix.centroids,
                   ix.part_order, ix.cent_code_vals, ix.cent_scales, ix.tc_rows, ix.tc_gstart,
-                  ix.tc_ids, ix.tc_norms, ix.tc_pmax, ix.assign};
+                  ix.tc_ids, ix.tc_norms, ix.tc_pmax, ix.assign, ix.sel_cb};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   ix = IndexData{};

@@ -788,6 +788,10 @@ void score_centroids(const IndexData& ix, const float* Qf, const float* qscale, 
 // Queries already prepared (Qf, row stride qstride); writes top [nq][t].
 void select_prepared(const IndexData& ix, const float* Qf, const float* qscale, int64_t nq, int qstride, int t,
                      int32_t* top, float* top_s, cudaStream_t s, Scratch& scr) {
+  if (!qscale && select_tc_usable(ix, Qf, qstride, t)) {
+    select_tc(ix, Qf, nq, qstride, t, top, top_s, s);   // scores and top-t fused on the tensor cores
+    return;
+  }
   float* S = scr.get<float>((size_t)nq * ix.c);
   score_centroids(ix, Qf, qscale, nq, qstride, S, s);
   if (t <= 32) {
@@ -907,6 +911,10 @@ void select_partitions_in(const IndexData& ix, const void* Q, soar_dtype dt, int
   float* S = reinterpret_cast<float*>(base);
   // every scratch element read below is first written here: nothing to clear
   prep_any(Q, dt, nq, ix.d, qstride, fp8, Qf, qscale, s);
+  if (!fp8 && select_tc_usable(ix, Qf, qstride, t)) {
+    select_tc(ix, Qf, nq, qstride, t, top, top_scores, s);   // needs no scratch beyond Qf
+    return;
+  }
   score_centroids(ix, Qf, qscale, nq, qstride, S, s);
   const int t2 = pow2_at_least(t);
   const int smem = t2 * 8 + (ix.c <= kToptSmemRow ? ix.c * 4 : 0);

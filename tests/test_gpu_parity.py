@@ -218,6 +218,39 @@ def test_select_partitions_matches(soar, tiny_index, t):
     np.testing.assert_allclose(sc.cpu().numpy(), wsc, rtol=1e-5, atol=1e-6)
 
 
+@pytest.fixture(scope="module")
+def select_index(soar):
+    """c = 200 centroids (three full 64-centroid tiles and a ragged one of 8),
+    d = 100 (query rows padded to 104 columns), centroids 3 and 150 and 199
+    identical (exact ties), built from the oracle's codebook."""
+    mix = synth.Mixture(100, 40, "isotropic", 0.3, param_seed=21)
+    X = mix.sample(4000, seed=22)
+    C = oracle.kmeans(X, synth.init_indices(4000, 200, seed=23), 2)
+    C[150] = C[3]
+    C[199] = C[3]
+    A = oracle.soar_assign(X, C, 1.0, 0)
+    ix = soar.soar_index_build(_t(X), _t(C), _t(A))
+    yield mix, C, ix
+    ix.close()
+
+
+@pytest.mark.parametrize("t", [1, 13, 16, 17, 32, 33])
+def test_select_partitions_tiles_and_tails(soar, select_index, t):
+    # 300 queries: two full 128-query blocks and a ragged one of 44
+    mix, C, ix = select_index
+    Q = mix.sample(300, seed=24 + t)
+    Q[7] = C[3] / np.linalg.norm(C[3])          # ranks the tied centroids first
+    top, sc = soar.soar_select_partitions(ix, _t(Q), t, with_scores=True)
+    want, wsc = oracle.select_partitions(Q, C, t)
+    exact = lambda q, p: np.asarray(C, np.float64)[np.asarray(p, np.int64)] @ Q[q].astype(np.float64)
+    top, sc = top.cpu().numpy(), sc.cpu().numpy()
+    assert topk_mismatches(top, want, wsc, exact) == []
+    np.testing.assert_allclose(sc, wsc, rtol=1e-5, atol=1e-6)
+    # equal scores keep the lower id first
+    assert list(top[7][: min(t, 3)]) == [3, 150, 199][: min(t, 3)]
+    assert sc[7][0] == sc[7][min(t, 3) - 1]
+
+
 @pytest.mark.parametrize("k,t", [(10, 4), (1, 1), (100, 8), (10, 64)])
 def test_search_matches_oracle(soar, tiny_index, k, t):
     X, Q, C, A, off, ids, ix = tiny_index
