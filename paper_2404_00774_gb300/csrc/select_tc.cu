@@ -147,22 +147,35 @@ __global__ void __launch_bounds__(kThreads, 1) select_tc_kernel(SelParams P) {
   const int nqb = (int)min((int64_t)kM, P.nq - q0);
   const int m = 32 * (warp & 3) + lane;   // epilogue: query slot = TMEM lane
 
-  // ---- queries -> hi / lo A operands (rows past the batch are zero)
+  // ---- queries -> hi / lo A operands (rows past the batch are zero); the
+  // row's loads go out 16 at a time so that their latencies overlap
   if (warp >= 3) {
     const float* q = P.Qf + (q0 + m) * (int64_t)P.qstride;
     const int64_t row = (int64_t)(m >> 3) * (8 * kp) + (m & 7) * 4;
-    for (int k4 = 0; k4 < kp / 4; ++k4) {
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (m < nqb && 4 * k4 < P.qstride) v = *reinterpret_cast<const float4*>(q + 4 * k4);
-      float e[4] = {v.x, v.y, v.z, v.w}, h[4], l[4];
+    constexpr int kBatch = 16;
+    for (int b0 = 0; b0 < kp / 4; b0 += kBatch) {
+      float4 v[kBatch];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const float x = 4 * k4 + u < P.d ? e[u] : 0.f;
-        h[u] = round_tf32(x);
-        l[u] = round_tf32(x - h[u]);
+      for (int u = 0; u < kBatch; ++u) {
+        const int k4 = b0 + u;
+        v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (m < nqb && k4 < kp / 4 && 4 * k4 < P.qstride) v[u] = *reinterpret_cast<const float4*>(q + 4 * k4);
       }
-      *reinterpret_cast<float4*>(sA + row + k4 * 32) = make_float4(h[0], h[1], h[2], h[3]);
-      *reinterpret_cast<float4*>(sA + a_bytes / 4 + row + k4 * 32) = make_float4(l[0], l[1], l[2], l[3]);
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        const int k4 = b0 + u;
+        if (k4 >= kp / 4) break;
+        const float e[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+        float h[4], l[4];
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          const float x = 4 * k4 + w < P.d ? e[w] : 0.f;
+          h[w] = round_tf32(x);
+          l[w] = round_tf32(x - h[w]);
+        }
+        *reinterpret_cast<float4*>(sA + row + k4 * 32) = make_float4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<float4*>(sA + a_bytes / 4 + row + k4 * 32) = make_float4(l[0], l[1], l[2], l[3]);
+      }
     }
     tc::fence_async_smem();
   }
