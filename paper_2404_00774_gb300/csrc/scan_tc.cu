@@ -287,13 +287,15 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
       float cut = gq;                                  // rows below cut cannot reach the top k
       int cnt = 0;
       bool ovf = false;
-      // register mode (KMAX > 0): the k best screened scores in registers and
-      // up to kCand candidates in shared memory.  Heap mode (KMAX == 0): the
-      // k best screened scores in a shared-memory min-heap and up to kc
-      // candidates in the slot's global list.
+      // register mode (KMAX > 0): the k best screened scores in the last k
+      // of KMAX registers (the first KMAX - k hold +inf, which no insertion
+      // passes, so the k-th best is always the last register) and up to
+      // kCand candidates in shared memory.  Heap mode (KMAX == 0): the k best
+      // screened scores in a shared-memory min-heap and up to kc candidates
+      // in the slot's global list.
       float ta[KMAX > 0 ? KMAX : 1];
 #pragma unroll
-      for (int j = 0; j < (KMAX > 0 ? KMAX : 1); ++j) ta[j] = -INFINITY;
+      for (int j = 0; j < (KMAX > 0 ? KMAX : 1); ++j) ta[j] = j < KMAX - k ? INFINITY : -INFINITY;
       float* cub = ext_s + m;                                              // [kCand][kM] scores
       int32_t* cpos = reinterpret_cast<int32_t*>(ext_s + kM * kCand) + m;   // [kCand][kM] padded rows
       float* heap = ext_s + m;                                             // heap mode: [k][kM]
@@ -349,42 +351,48 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
                   g[j2] = desc ? fminf(x, y) : fmaxf(x, y);
                 }
               }
-          float seed = g[0];
+          // the k-th largest = the smallest of the first k (g is sorted)
+          float seed = INFINITY;
 #pragma unroll
           for (int j2 = 0; j2 < 16; ++j2)
-            if (j2 == k - 1) seed = g[j2];
+            if (j2 < k) seed = fminf(seed, g[j2]);
           floor_ = seed;
           cut = fmaxf(seed - 2.f * dlt, gq);
         }
         // register-only screen against the cut at the tile's start (the cut
-        // only rises, so this keeps a superset); survivors parked in smem
-        uint64_t mask = 0;
+        // only rises, so this keeps a superset); survivors parked in smem.
+        // An idle slot screens against +inf; the bits of a short last tile's
+        // missing rows are cleared afterwards.  Four independent 16-column
+        // masks keep the OR chains short.
+        const float cut0 = active ? cut : INFINITY;
+        uint32_t mq[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
         for (int c = 0; c < kN; ++c) {
           const float a = __uint_as_float(c < 32 ? r0[c & 31] : r1[c & 31]);
-          if (active && c < nvalid && a >= cut) {
-            mask |= (uint64_t)1 << c;
+          if (a >= cut0) {
+            mq[c >> 4] |= 1u << (c & 31);
             av_s[c * kM + m] = a;
           }
         }
-        // pass 1: the tile's survivors raise the k best screened scores
-        for (uint64_t m1 = mask; m1; m1 &= m1 - 1) {
-          const int c = __ffsll((long long)m1) - 1;
+        uint64_t mask = (uint64_t)(mq[0] | mq[1]) | ((uint64_t)(mq[2] | mq[3]) << 32);
+        if (nvalid < kN) mask &= ((uint64_t)1 << nvalid) - 1;
+        // one pass over the survivors in row order: each raises the k best
+        // screened scores, then joins the candidates if it still reaches the
+        // (risen) cut; the item's final cut filters the list at the end
+        for (; mask; mask &= mask - 1) {
+          const int c = __ffsll((long long)mask) - 1;
           const float a = av_s[c * kM + m];
+          if (a < cut) continue;
           if constexpr (KMAX > 0) {
             if (a > ak) {
               float v = a;
 #pragma unroll
               for (int j = 0; j < KMAX; ++j) {
-                if (j < k) {
-                  const float hi = fmaxf(ta[j], v);
-                  v = fminf(ta[j], v);
-                  ta[j] = hi;
-                }
+                const float hi = fmaxf(ta[j], v);
+                v = fminf(ta[j], v);
+                ta[j] = hi;
               }
-#pragma unroll
-              for (int j = 0; j < KMAX; ++j)
-                if (j == k - 1) ak = ta[j];
+              ak = ta[KMAX > 0 ? KMAX - 1 : 0];
             }
           } else {
             if (hn < k) {                            // heap not full: sift the new score up
@@ -416,13 +424,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
               ak = heap[0];
             }
           }
-        }
-        if (refresh) gq = fmaxf(gq, unordered(gload) - dlt);
-        cut = fmaxf(fmaxf(ak, floor_) - 2.f * dlt, gq);   // s~ + dlt < max(L_k, G_q)  <=>  s~ < cut
-        // pass 2: keep the rows that survive the tile's final cut
-        for (; mask; mask &= mask - 1) {
-          const int c = __ffsll((long long)mask) - 1;
-          const float a = av_s[c * kM + m];
+          cut = fmaxf(fmaxf(ak, floor_) - 2.f * dlt, gq);   // s~ + dlt < max(L_k, G_q)  <=>  s~ < cut
           if (a < cut) continue;
           if constexpr (KMAX > 0) {
             if (cnt == kCand) {                      // drop candidates that fell below the cut
@@ -450,6 +452,10 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
             if (cnt < P.kc) glist[cnt++] = Cand{a, pr0 + c};
             else ovf = true;
           }
+        }
+        if (refresh) {
+          gq = fmaxf(gq, unordered(gload) - dlt);
+          cut = fmaxf(cut, gq);
         }
       }
       if (active && !abort_s) {

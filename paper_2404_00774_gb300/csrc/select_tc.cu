@@ -27,7 +27,7 @@
 // lane.  Each epilogue thread keeps its query's t best (score, id) in
 // registers; a tile's 64 scores are screened 16 at a time against the
 // current t-th best, the survivors parked in shared memory and inserted.
-// Columns arrive in ascending id order and only a strictly better key is
+// Columns arrive in ascending id order and only a strictly larger score is
 // inserted, so equal scores keep the lower centroid id first (the order of
 // the other selection kernels: score descending, id ascending).
 // Every mbarrier wait is bounded (about a second); on expiry the CTA raises
@@ -88,15 +88,6 @@ struct SelParams {
   int* err;           // set to 1 when a wait expired
 };
 
-// Ordered key of a float (larger float -> larger unsigned key) and back.
-__device__ __forceinline__ uint32_t okey(float f) {
-  const uint32_t u = __float_as_uint(f);
-  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-}
-__device__ __forceinline__ float okey_float(uint32_t k) {
-  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
-}
-
 template <int TMAX>
 __global__ void __launch_bounds__(kThreads, 1) select_tc_kernel(SelParams P) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -109,7 +100,7 @@ __global__ void __launch_bounds__(kThreads, 1) select_tc_kernel(SelParams P) {
   const uint32_t b_bytes = 2u * b_part;
   float* sA = reinterpret_cast<float*>(base);                        // hi, then lo at + a_bytes
   float* sB = reinterpret_cast<float*>(base + 2 * a_bytes);          // kStages x (hi, lo)
-  uint32_t* park = reinterpret_cast<uint32_t*>(base + 2 * a_bytes + kStages * b_bytes);  // [kChunk][kM]
+  float* park = reinterpret_cast<float*>(base + 2 * a_bytes + kStages * b_bytes);  // [kChunk][kM]
   uint64_t* bars = reinterpret_cast<uint64_t*>(park + kChunk * kM);  // full[2], empty[2], tfull[2], tempty[2]
   __shared__ uint32_t tmem_base_s;
   __shared__ int abort_s;
@@ -233,17 +224,17 @@ __global__ void __launch_bounds__(kThreads, 1) select_tc_kernel(SelParams P) {
       if (tc::named_bar_or(2, 64, !ok)) break;
     }
   } else {
-    // ---- epilogue: the query's t best (ordered score key, centroid id) in
-    // the last t of TMAX slots, best first; the first TMAX - t slots hold the
-    // largest key, which no insertion passes, so the t-th best always sits
-    // in the last slot (a fixed register)
+    // ---- epilogue: the query's t best (score, centroid id) in the last t
+    // of TMAX slots, best first; the first TMAX - t slots hold +inf, which no
+    // insertion passes, so the t-th best always sits in the last slot (a
+    // fixed register)
     const bool active = m < nqb;
     const int lead = TMAX - t;
-    uint32_t ts[TMAX];
+    float ts[TMAX];
     int ti[TMAX];
 #pragma unroll
-    for (int j = 0; j < TMAX; ++j) { ts[j] = j < lead ? 0xffffffffu : 0u; ti[j] = -1; }
-    uint32_t cut = 0u;                               // the t-th best key (0 until t are held)
+    for (int j = 0; j < TMAX; ++j) { ts[j] = j < lead ? INFINITY : -INFINITY; ti[j] = -1; }
+    float cut = -INFINITY;                           // the t-th best score (-inf until t are held)
     for (int i = 0; i < ntiles; ++i) {
       const uint32_t b = i & 1, tph = (i >> 1) & 1;
       const bool ok = tc::bar_wait(tfull(b), tph, abort_v);
@@ -264,26 +255,31 @@ __global__ void __launch_bounds__(kThreads, 1) select_tc_kernel(SelParams P) {
       const int nvalid = min(kN, P.c - col0);
 #pragma unroll
       for (int ch = 0; ch < kN / kChunk; ++ch) {
-        // screen 16 columns against the cut; survivors parked in smem
-        uint32_t mask = 0;
+        // screen 16 columns against the cut (+inf for an idle slot; columns
+        // past c are cleared afterwards); survivors parked in smem
+        const float cut0 = active ? cut : INFINITY;
+        uint32_t mk0 = 0, mk1 = 0;
 #pragma unroll
         for (int cc = 0; cc < kChunk; ++cc) {
           const int c = ch * kChunk + cc;
-          const uint32_t key = okey(__uint_as_float(c < 32 ? r0[c & 31] : r1[c & 31]));
-          if (active && c < nvalid && key > cut) {
-            mask |= 1u << cc;
-            park[cc * kM + m] = key;
+          const float v = __uint_as_float(c < 32 ? r0[c & 31] : r1[c & 31]);
+          if (v > cut0) {
+            if (cc < kChunk / 2) mk0 |= 1u << cc;
+            else mk1 |= 1u << cc;
+            park[cc * kM + m] = v;
           }
         }
+        uint32_t mask = mk0 | mk1;
+        if (nvalid < kN) mask &= ch * kChunk >= nvalid ? 0u : nvalid - ch * kChunk >= 32 ? ~0u : (1u << (nvalid - ch * kChunk)) - 1;
         for (; mask; mask &= mask - 1) {
           const int cc = __ffs(mask) - 1;
-          uint32_t v = park[cc * kM + m];
-          if (v <= cut) continue;
+          float v = park[cc * kM + m];
+          if (!(v > cut)) continue;
           int id = col0 + ch * kChunk + cc;
 #pragma unroll
           for (int j = 0; j < TMAX; ++j) {
             const bool gt = v > ts[j];
-            const uint32_t tv = ts[j];
+            const float tv = ts[j];
             const int tid = ti[j];
             ts[j] = gt ? v : tv;
             ti[j] = gt ? id : tid;
@@ -299,10 +295,11 @@ __global__ void __launch_bounds__(kThreads, 1) select_tc_kernel(SelParams P) {
 #pragma unroll
       for (int j = 0; j < TMAX; ++j) {
         if (j >= lead) {
-          // an entry stays empty only for keys no score reaches (NaN rows):
+          // an entry stays empty only when fewer than t scores exceed -inf
+          // (NaN or -inf rows):
           // keep the ids valid partitions all the same
           P.top[q * t + j - lead] = ti[j] >= 0 ? ti[j] : j - lead;
-          if (P.top_s) P.top_s[q * t + j - lead] = okey_float(ts[j]);
+          if (P.top_s) P.top_s[q * t + j - lead] = ts[j];
         }
       }
     }
