@@ -112,6 +112,35 @@ __device__ __forceinline__ uint64_t rank_key(float score, uint32_t id) {
   return ((uint64_t)(~float_key(score)) << 32) | (uint64_t)id;
 }
 
+// Exclusive scan of one value per thread across the block (all threads of
+// the block call it; blockDim.x a multiple of 32); `total` gets the sum.
+template <typename T>
+__device__ T block_exclusive_scan(T v, T* smem_warp /*[32]*/, T& total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  T x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) smem_warp[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    T s = lane < nw ? smem_warp[lane] : T(0);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      T y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    smem_warp[lane] = s;  // inclusive scan of warp totals
+  }
+  __syncthreads();
+  T warp_base = w > 0 ? smem_warp[w - 1] : T(0);
+  total = smem_warp[nw - 1];
+  __syncthreads();
+  return warp_base + x - v;
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll

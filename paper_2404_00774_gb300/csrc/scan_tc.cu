@@ -128,8 +128,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
   // per-slot arrays are interleaved slot-fastest ([entry][kM]) so that the 32
   // lanes of a warp always touch 32 distinct banks
   float* ext_s = av_s + kN * kM;   // candidates [kCand][kM] (+ rows) or the heap [k][kM]
-  float* qn_s = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(ext_s) + ext_bytes(k));  // [kM]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(qn_s + kM);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(ext_s) + ext_bytes(k));
   // bars: full[S], empty[S], tfull[2], tempty[2]
   __shared__ uint32_t tmem_base_s;
   __shared__ ItemDesc item_s;
@@ -198,17 +197,24 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
     // ---- queries of the item -> A operand (row m of the epilogue threads),
     // staged by 16-byte cp.async so that the row's loads are all in flight
     // at once; the producer warp is not held by this barrier and already
-    // streams the item's tiles
+    // streams the item's tiles.  The epilogue's per-slot inputs (query id,
+    // its published bound, its norm, the partition's largest row norm) are
+    // loaded meanwhile, off the first tile's critical path.
+    int64_t qid_pre = 0;
+    unsigned gb_pre = 0u;
+    float qn_pre = 0.f, pmax_pre = 0.f;
     if (warp >= 3) {
       float* arow = sA + (m >> 3) * (kp * 8) + (m & 7) * 4;
+      pmax_pre = P.pmax[p];
       if (jq < nqi) {
         const int64_t qi = P.work.query(e0 + jq);
         const float* q = P.Qf + qi * (int64_t)kp;
         for (int k4 = 0; k4 < kp / 4; ++k4) tc::cp_async16(tc::smem_u32(arow + k4 * 32), q + 4 * k4);
-        qn_s[m] = P.qnorm[qi];
+        qid_pre = qi;
+        qn_pre = P.qnorm[qi];
+        gb_pre = __ldcg(P.gbound + qi);
       } else {
         for (int k4 = 0; k4 < kp / 4; ++k4) *reinterpret_cast<float4*>(arow + k4 * 32) = make_float4(0.f, 0.f, 0.f, 0.f);
-        qn_s[m] = 0.f;
       }
       tc::cp_async_wait_all();
       tc::fence_async_smem();
@@ -276,12 +282,11 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
     } else {
       // ---- epilogue: screening bounds and candidate rows per query
       const bool active = jq < nqi;
-      const float qn = qn_s[m];
-      const float dlt = ldexpf(qn, -8) * P.pmax[p];   // |s~ - exact| < dlt / 2 for every row of p
+      const float dlt = ldexpf(qn_pre, -8) * pmax_pre;   // |s~ - exact| < dlt / 2 for every row of p
       // G_q, published by this query's finished partitions, bounds its final
       // k-th best exact score from below: rows with s~ + dlt < G_q cannot count
-      const int64_t qid = active ? P.work.query(e0 + jq) : 0;
-      float gq = active ? unordered(__ldcg(P.gbound + qid)) - dlt : -INFINITY;
+      const int64_t qid = qid_pre;
+      float gq = active ? unordered(gb_pre) - dlt : -INFINITY;
       float ak = -INFINITY;                            // k-th best screened score (-inf until k seen)
       float floor_ = -INFINITY;                        // a lower bound of the k-th best screened score
       float cut = gq;                                  // rows below cut cannot reach the top k
@@ -379,10 +384,8 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
         // one pass over the survivors in row order: each raises the k best
         // screened scores, then joins the candidates if it still reaches the
         // (risen) cut; the item's final cut filters the list at the end
-        for (; mask; mask &= mask - 1) {
-          const int c = __ffsll((long long)mask) - 1;
-          const float a = av_s[c * kM + m];
-          if (a < cut) continue;
+        auto survivor = [&](const int c, const float a) {
+          if (a < cut) return;
           if constexpr (KMAX > 0) {
             if (a > ak) {
               float v = a;
@@ -425,7 +428,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
             }
           }
           cut = fmaxf(fmaxf(ak, floor_) - 2.f * dlt, gq);   // s~ + dlt < max(L_k, G_q)  <=>  s~ < cut
-          if (a < cut) continue;
+          if (a < cut) return;
           if constexpr (KMAX > 0) {
             if (cnt == kCand) {                      // drop candidates that fell below the cut
               int w = 0;
@@ -452,6 +455,10 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
             if (cnt < P.kc) glist[cnt++] = Cand{a, pr0 + c};
             else ovf = true;
           }
+        };
+        for (; mask; mask &= mask - 1) {
+          const int c = __ffsll((long long)mask) - 1;
+          survivor(c, av_s[c * kM + m]);
         }
         if (refresh) {
           gq = fmaxf(gq, unordered(gload) - dlt);
@@ -499,7 +506,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
 
 size_t smem_bytes(int kp, int k, int stages) {
   return 1024 + (size_t)kM * kp * 4 + (size_t)stages * kN * kp * 4 + (size_t)kN * kM * 4 + ext_bytes(k) +
-         (size_t)kM * 4 + (size_t)(2 * stages + 4) * 8;
+         (size_t)(2 * stages + 4) * 8;
 }
 
 int pick_stages(int kp, int k) {

@@ -80,9 +80,10 @@ template <> struct Expand<uint8_t> {
 
 // Warp per query.  Plain: fp32 copy padded with zeros to `stride`.
 // FP8: code values of e4m3(q / scale), scale = max|q| / 448.
+// qnorm (optional): ||row|| of the written row.
 template <typename QT>
 __global__ void prep_queries(const QT* __restrict__ Q, int64_t nq, int d, int stride, bool fp8,
-                             float* __restrict__ Qf, float* __restrict__ qscale) {
+                             float* __restrict__ Qf, float* __restrict__ qscale, float* __restrict__ qnorm) {
   int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (q >= nq) return;
@@ -96,13 +97,19 @@ __global__ void prep_queries(const QT* __restrict__ Q, int64_t nq, int d, int st
     for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
     scale = amax > 0.f ? amax / 448.f : 1.f;
   }
+  float acc = 0.f;
   for (int k = lane; k < stride; k += 32) {
     float v = k < d ? load_elem(src, k) : 0.f;
     if (fp8 && k < d)
       v = fp8_value((uint8_t)__nv_cvt_float_to_fp8(v / scale, __NV_SATFINITE, __NV_E4M3));
     dst[k] = v;
+    acc = fmaf(v, v, acc);
   }
   if (fp8 && lane == 0) qscale[q] = scale;
+  if (qnorm) {
+    acc = warp_sum(acc);
+    if (lane == 0) qnorm[q] = sqrtf(acc);
+  }
 }
 
 // ------------------------------------------------------------ centroid scores
@@ -410,14 +417,54 @@ __global__ void pair_scatter(const int32_t* __restrict__ top, int64_t nq, int tm
   inv[e] = (int32_t)pos;
 }
 
-__global__ void item_counts(const int64_t* __restrict__ pair_off, const int32_t* __restrict__ order, int c,
-                            int qb, int32_t* __restrict__ cnt) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i > c) return;
-  if (i == c) { cnt[c] = 0; return; }
-  int p = order[i];
-  int64_t m = pair_off[p + 1] - pair_off[p];
-  cnt[i] = (int32_t)((m + qb - 1) / qb);
+// One block: the offsets of the grouped pairs and of the work items.
+//   pair_off[0 .. c+2)  exclusive scan of the per-partition pair counts
+//   item_base[0 .. c+1) exclusive scan of ceil(pairs / qb) over the
+//                       partitions in `order` (the last entry: the total)
+//   cursor[0 .. c+1)    zeroed for pair_scatter
+// Each thread takes a run of consecutive entries, so one block scan covers
+// any c.
+constexpr int kOffThreads = 1024;
+__global__ void __launch_bounds__(kOffThreads) group_offsets(const unsigned long long* __restrict__ cnt, int c,
+                                                             const int32_t* __restrict__ order, int qb,
+                                                             int64_t* __restrict__ pair_off,
+                                                             int32_t* __restrict__ item_base,
+                                                             int32_t* __restrict__ cursor) {
+  __shared__ int64_t warp64[32];
+  __shared__ int32_t warp32[32];
+  const int tid = threadIdx.x;
+  {
+    const int n = c + 2, per = (n + kOffThreads - 1) / kOffThreads;
+    const int i0 = min(n, tid * per), i1 = min(n, i0 + per);
+    int64_t sum = 0;
+    for (int i = i0; i < i1; ++i) sum += (int64_t)cnt[i];
+    int64_t total;
+    int64_t run = block_exclusive_scan<int64_t>(sum, warp64, total);
+    for (int i = i0; i < i1; ++i) {
+      pair_off[i] = run;
+      run += (int64_t)cnt[i];
+    }
+  }
+  __syncthreads();                       // pair_off complete and visible to the block
+  {
+    const int n = c + 1, per = (n + kOffThreads - 1) / kOffThreads;
+    const int i0 = min(n, tid * per), i1 = min(n, i0 + per);
+    auto items = [&](int i) -> int32_t {
+      if (i == c) return 0;
+      const int p = order[i];
+      const int64_t m = pair_off[p + 1] - pair_off[p];
+      return (int32_t)((m + qb - 1) / qb);
+    };
+    int32_t sum = 0;
+    for (int i = i0; i < i1; ++i) sum += items(i);
+    int32_t total;
+    int32_t run = block_exclusive_scan<int32_t>(sum, warp32, total);
+    for (int i = i0; i < i1; ++i) {
+      item_base[i] = run;
+      run += items(i);
+      cursor[i] = 0;
+    }
+  }
 }
 
 // ------------------------------------------------------------ scan
@@ -748,15 +795,16 @@ void launch_scan(const Work& work, int step_nrc, int max_items, const RowT* rows
 }
 
 template <typename QT>
-void prep(const QT* Q, int64_t nq, int d, int stride, bool fp8, float* Qf, float* qscale, cudaStream_t s) {
-  prep_queries<QT><<<ceil_div(nq * 32, 256), 256, 0, s>>>(Q, nq, d, stride, fp8, Qf, qscale);
+void prep(const QT* Q, int64_t nq, int d, int stride, bool fp8, float* Qf, float* qscale, float* qnorm,
+          cudaStream_t s) {
+  prep_queries<QT><<<ceil_div(nq * 32, 256), 256, 0, s>>>(Q, nq, d, stride, fp8, Qf, qscale, qnorm);
   SOAR_LAUNCHED();
 }
 
 void prep_any(const void* Q, soar_dtype dt, int64_t nq, int d, int stride, bool fp8, float* Qf, float* qscale,
-              cudaStream_t s) {
-  if (dt == SOAR_F32) prep<float>(static_cast<const float*>(Q), nq, d, stride, fp8, Qf, qscale, s);
-  else prep<__nv_bfloat16>(static_cast<const __nv_bfloat16*>(Q), nq, d, stride, fp8, Qf, qscale, s);
+              cudaStream_t s, float* qnorm = nullptr) {
+  if (dt == SOAR_F32) prep<float>(static_cast<const float*>(Q), nq, d, stride, fp8, Qf, qscale, qnorm, s);
+  else prep<__nv_bfloat16>(static_cast<const __nv_bfloat16*>(Q), nq, d, stride, fp8, Qf, qscale, qnorm, s);
 }
 
 int pow2_at_least(int v) {
@@ -824,19 +872,16 @@ Grouped group_pairs(const IndexData& ix, int64_t nq, int t, const int32_t* tpq, 
   unsigned long long* cnt = scr.get<unsigned long long>((size_t)c + 2);
   int32_t* cursor = scr.get<int32_t>((size_t)c + 1);
   SOAR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * (c + 2), s));
-  SOAR_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int32_t) * (c + 1), s));
   pair_counts<<<ceil_div(P, 256), 256, 0, s>>>(top, nq, t, tpq, c, cnt);
   SOAR_LAUNCHED();
   Grouped g;
   g.pair_off = scr.get<int64_t>((size_t)c + 2);
-  exclusive_scan_i64(reinterpret_cast<const int64_t*>(cnt), g.pair_off, (int64_t)c + 2, s, scr);
+  g.item_base = scr.get<int32_t>((size_t)c + 1);
+  group_offsets<<<1, kOffThreads, 0, s>>>(cnt, c, ix.part_order, qb, g.pair_off, g.item_base, cursor);
+  SOAR_LAUNCHED();
   int32_t* vals = scr.get<int32_t>(P);
   pair_scatter<<<ceil_div(P, 256), 256, 0, s>>>(top, nq, t, tpq, c, g.pair_off, cursor, vals, inv);
   SOAR_LAUNCHED();
-  g.item_base = scr.get<int32_t>((size_t)c + 1);
-  item_counts<<<ceil_div((int64_t)c + 1, 256), 256, 0, s>>>(g.pair_off, ix.part_order, c, qb, g.item_base);
-  SOAR_LAUNCHED();
-  exclusive_scan_i32(g.item_base, g.item_base, (int64_t)c + 1, s, scr);
   stage_mark(s, "group", false);
   g.vals = vals;
   g.max_items = (int)std::min<int64_t>(P / qb + c + 1, 1 << 30);
@@ -852,20 +897,6 @@ void ivf_scan_typed(const IndexData& ix, const float* Qf, const float* qscale, i
   IvfWork work{ix.offsets, g.pair_off, g.vals, ix.part_order, g.item_base, ix.c, t, qb};
   launch_scan<RowT, IvfWork>(work, 1, g.max_items, static_cast<const RowT*>(ix.vectors), ix.row_stride, ix.ids,
                              ix.row_scales, Qf, qscale, len, qb, partials, s, scr);
-}
-
-// ||q|| of every prepared query row (warp per query).
-__global__ void query_norms(const float* __restrict__ Qf, int64_t nq, int stride, float* __restrict__ qn) {
-  const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (q >= nq) return;
-  float acc = 0.f;
-  for (int k = lane; k < stride; k += 32) {
-    const float v = Qf[q * stride + k];
-    acc = fmaf(v, v, acc);
-  }
-  acc = warp_sum(acc);
-  if (lane == 0) qn[q] = sqrtf(acc);
 }
 
 }  // namespace
@@ -933,9 +964,7 @@ void search(const IndexData& ix, const void* Q, soar_dtype dt, int64_t nq, int32
     float* Qf = scr.get<float>((size_t)nq * qstride);
     float* qn = scr.get<float>(nq);
     stage_mark(s, "select", true);
-    prep_any(Q, dt, nq, ix.d, qstride, false, Qf, nullptr, s);
-    query_norms<<<ceil_div(nq * 32, 256), 256, 0, s>>>(Qf, nq, qstride, qn);
-    SOAR_LAUNCHED();
+    prep_any(Q, dt, nq, ix.d, qstride, false, Qf, nullptr, s, qn);   // rows and their norms
     int32_t* top = scr.get<int32_t>((size_t)nq * t);
     select_prepared(ix, Qf, nullptr, nq, qstride, t, top, nullptr, s, scr);
     stage_mark(s, "select", false);

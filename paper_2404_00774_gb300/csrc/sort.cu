@@ -12,34 +12,6 @@ constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
-// Exclusive scan of one value per thread across the block; returns the total.
-template <typename T>
-__device__ T block_exclusive_scan(T v, T* smem_warp /*[32]*/, T& total) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  T x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    T y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) smem_warp[w] = x;
-  __syncthreads();
-  if (w == 0) {
-    T s = lane < nw ? smem_warp[lane] : T(0);
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      T y = __shfl_up_sync(0xffffffffu, s, o);
-      if (lane >= o) s += y;
-    }
-    smem_warp[lane] = s;  // inclusive scan of warp totals
-  }
-  __syncthreads();
-  T warp_base = w > 0 ? smem_warp[w - 1] : T(0);
-  total = smem_warp[nw - 1];
-  __syncthreads();
-  return warp_base + x - v;
-}
-
 template <typename T>
 __global__ void __launch_bounds__(kScanThreads) scan_tile_sums(const T* in, T* sums, int64_t count) {
   __shared__ T warp[32];
