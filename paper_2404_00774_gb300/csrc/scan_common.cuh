@@ -49,6 +49,23 @@ struct IvfWork {
   __device__ int64_t slot(int64_t e) const { return e; }
 };
 
+// Largest k of the tensor-core scan (its heap mode) and the largest
+// candidate list per pair slot in that mode.
+constexpr int kTcWideK = 128;
+constexpr int kTcWideList = 256;
+
+// Finishing of the tensor-core scan (finish_tc.cu), on the scan's candidate
+// lists [nq * t][kc] and headers [nq * t] (L_k, count | overflow << 31):
+// for k <= 32 the exact top k of every query into ids_out / scores_out;
+// for k <= 128 every pair slot's list rescored exactly in place (best
+// first, an id of -1 closing a shorter list) for the caller's merge.
+void finish_tc_queries(const IndexData& ix, const Cand* lists, const int2* hdr, const int32_t* inv, int64_t nq,
+                       int t, const int32_t* tpq, const float* Qf, const int32_t* top, int k, int kc,
+                       int64_t* ids_out, float* scores_out, cudaStream_t s);
+void rescore_tc_wide(const IndexData& ix, Cand* lists, const int2* hdr, const int32_t* inv,
+                     const int32_t* pair_vals, int64_t nq, int t, const int32_t* tpq, const float* Qf,
+                     const int32_t* top, int k, int kc, cudaStream_t s, Scratch& scr);
+
 // Tensor-core scan (scan_tc.cu) of a fp32 index (rows in the core-matrix
 // layout of tc.cuh, queries as fp32 rows of tc_kp columns): screening on the
 // tensor cores, then exact rescoring.  For k <= 32 it also merges: the
