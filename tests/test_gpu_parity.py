@@ -263,6 +263,34 @@ def test_search_matches_oracle(soar, tiny_index, k, t):
     assert mx < 1e-5, (mx, mean)
 
 
+@pytest.fixture(scope="module")
+def wide_index(soar):
+    """c = 1 500 centroids: the kernel that lays out the grouped (query,
+    probe) pairs then gives each of its threads a run of two partitions
+    (c + 2 > 1 024); built from the oracle's codebook and assignment."""
+    mix = synth.Mixture(32, 60, "isotropic", 0.3, param_seed=31)
+    X = mix.sample(30000, seed=32)
+    C = oracle.kmeans(X, synth.init_indices(30000, 1500, seed=33), 2)
+    A = oracle.soar_assign(X, C, 1.0, 1)
+    off, ids = oracle.build_ivf(A, C.shape[0])
+    ix = soar.soar_index_build(_t(X), _t(C), _t(A))
+    yield mix, X, C, off, ids, ix
+    ix.close()
+
+
+@pytest.mark.parametrize("k,t", [(10, 8), (10, 40)])
+def test_search_many_partitions_matches_oracle(soar, wide_index, k, t):
+    mix, X, C, off, ids, ix = wide_index
+    Q = mix.sample(150, seed=34)
+    gi, gs = soar.soar_search(ix, _t(Q), k, t)
+    wi, ws = oracle.ivf_search(Q, X, C, off, ids, k, t)
+    gi, gs = gi.cpu().numpy(), gs.cpu().numpy()
+    ex = _exact(X, Q)
+    assert topk_mismatches(gi, wi, ws, ex) == []
+    mx, mean = score_errors(gi, gs, ex)
+    assert mx < 1e-5, (mx, mean)
+
+
 def test_search_all_partitions_is_brute_force(soar, tiny_index):
     X, Q, C, A, off, ids, ix = tiny_index
     gi, gs = soar.soar_search(ix, _t(Q), 10, C.shape[0])
