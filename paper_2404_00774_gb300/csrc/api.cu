@@ -43,6 +43,10 @@ void stage_mark(cudaStream_t s, const char* stage, bool begin) {
 }
 
 namespace {
+// The device error word: a static device variable (zero at module load), so
+// that no call, the allocation-free ones included, allocates it.  Its device
+// address is looked up once per device with cudaGetSymbolAddress.
+__device__ int g_err_dev;
 std::mutex g_err_mu;
 int* g_err_word[256] = {};
 }  // namespace
@@ -53,10 +57,9 @@ int* device_error_word() {
   if (dev < 0 || dev >= 256) fail(SOAR_EUNSUPPORTED, "device ordinal above 255");
   std::lock_guard<std::mutex> lock(g_err_mu);
   if (!g_err_word[dev]) {
-    int* p = nullptr;
-    SOAR_CUDA(cudaMalloc(&p, sizeof(int)));
-    SOAR_CUDA(cudaMemset(p, 0, sizeof(int)));
-    g_err_word[dev] = p;
+    void* p = nullptr;
+    SOAR_CUDA(cudaGetSymbolAddress(&p, g_err_dev));
+    g_err_word[dev] = static_cast<int*>(p);
   }
   return g_err_word[dev];
 }
