@@ -164,7 +164,10 @@ SOAR_API soar_status soar_index_free(soar_index* index);
  *   top_out   [nq][t] int32 partition ids
  *   score_out [nq][t] fp32 scores, may be NULL
  * Scores are fp32 (SOAR_SCORE_F32 indices) or FP8-scaled (SOAR_SCORE_FP8).
- * Requires 1 <= t <= min(c, 8192).
+ * Ties go to the lower partition id.  For t <= 32 on fp32 centroids with d <= 104
+ * the scores come from the tensor cores with each fp32 value split into two
+ * tf32 parts (three products), an error within that of a fp32 dot product;
+ * otherwise from a fp32 GEMM.  Requires 1 <= t <= min(c, 8192).
  */
 SOAR_API soar_status soar_select_partitions(const soar_index* index, const void* Q, soar_dtype dtype,
                                    int64_t nq, int32_t t, int32_t* top_out, float* score_out,
@@ -216,7 +219,8 @@ SOAR_API soar_status soar_quantize_fp8(const void* V, soar_dtype dtype, int64_t 
  * soar_select_partitions.
  *
  * Scratch (the queries' padded rows and the nq x c score matrix, at most
- * SOAR_STATIC_SCRATCH_BYTES) lives in a fixed device array inside this
+ * SOAR_STATIC_SCRATCH_BYTES; the limit is checked on that size even when the
+ * tensor-core selection needs no score matrix) lives in a fixed device array inside this
  * library: every GPU that loads the library holds those bytes until the
  * process exits.  A batch that needs more returns SOAR_EINVAL with the
  * byte count in soar_last_error(); split it into smaller calls.  The first
