@@ -160,6 +160,23 @@ def find_t(sb, index, Qd, truth, k, t_max):
     return lo, rec(lo)
 
 
+def shard_queries(Qall, rank, nq):
+    """Rank `rank`'s queries: its own consecutive block of nq (weak scaling:
+    every rank searches nq queries; the blocks are disjoint)."""
+    return Qall[rank * nq:(rank + 1) * nq]
+
+
+def max_over_ranks(value, dist=None, device=None):
+    """The largest of every rank's `value` (the job's time is its slowest
+    rank's); the value itself on one process."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def kernel_hash():
     h = hashlib.sha256()
     with open(os.path.join(ROOT, "paper_2404_00774_gb300", "csrc", "scan_tc.cu"), "rb") as f:
@@ -357,7 +374,7 @@ def run_ours(args):
     mix = synth.mixture_for(w)
     X = mix.sample(w.n, w.data_seed)
     Qall = mix.sample(nq * world, w.query_seed)
-    Q = Qall[rank * nq:(rank + 1) * nq]          # queries are sharded across ranks
+    Q = shard_queries(Qall, rank, nq)            # queries are sharded across ranks
     init = synth.init_indices(w.n, w.c, w.init_seed)
     log(f"[bench] data {time.perf_counter() - t0:.1f}s")
     Xd = torch.from_numpy(X).to(dev)
@@ -447,11 +464,7 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     stages = sb.soar_stage_times()
-    ms_step = statistics.mean(ts)
-    if dist:
-        tt = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_step = float(tt)
+    ms_step = max_over_ranks(statistics.mean(ts), dist, dev)
     results["soar"]["qps"] = nq / (ms_step / 1e3)
 
     # ---- e2e: pinned host queries in, results out, through the same call
@@ -468,12 +481,15 @@ def run_ours(args):
 
     for _ in range(2):
         e2e_once()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     e2e_ts = []
     for i in range(max(3, args.steps // 2)):
         flush.fill_(float(i))
         (_, ms) = timed(e2e_once)
         e2e_ts.append(ms)
-    e2e_ms = statistics.mean(e2e_ts)
+    e2e_ms = max_over_ranks(statistics.mean(e2e_ts), dist, dev)
 
     # ---- roofline of the dominant kernel (the partition scan)
     hbm, bf16, peak_src = peaks()
