@@ -438,3 +438,117 @@ def test_mlp_adam_matches_hand_update():
     probe_mlp.adam_step(p, g, m, v, 1, 0.1)
     # first Adam step moves each parameter by lr * sign(g) (bias corrected)
     assert p["W1"][0, 0] == pytest.approx(1.0 - 0.1, rel=1e-6)
+
+
+# ------------------------------------- FP8 shortlist on exactly encodable rows
+
+def _fp8_exact_rows(rng, m, d, big):
+    """Rows s_i * c_i with integer c_i in [-13, 13] plus one entry of +-14 and
+    a power-of-two s_i: max|row| = 14 s_i, so the per-row scale is s_i / 32,
+    the codes are 32 c_i (integers times 32 below 16 * 32 are E4M3 values) and
+    the FP8 form of every row is exact.  ``big`` sets the spread of s_i."""
+    c = rng.integers(-13, 14, size=(m, d)).astype(np.float64)
+    c[np.arange(m), rng.integers(0, d, size=m)] = 14.0 * rng.choice([-1.0, 1.0], size=m)
+    s = 2.0 ** rng.integers(-big, 1, size=m).astype(np.float64)
+    return (c * s[:, None]).astype(np.float32)
+
+
+def test_fp8_exact_rows_are_fixed_points():
+    rng = np.random.default_rng(40)
+    R = _fp8_exact_rows(rng, 50, 9, 3)
+    codes, scale = oracle.quantize_rows_fp8(R)
+    np.testing.assert_array_equal(codes.astype(np.float64) * scale[:, None].astype(np.float64),
+                                  R.astype(np.float64))
+
+
+@pytest.mark.parametrize("rescore", [10, 25])
+def test_precision_search_equals_exact_search_when_fp8_is_exact(rescore):
+    # With every query, centroid and row exactly representable in the scaled
+    # FP8 form, the approximate scores are the exact ones: the FP8 partition
+    # choice and the FP8 shortlist (even one of k entries) rank exactly as the
+    # fp64 search does, so precision_search must return ivf_search's top k id
+    # for id.  Row scales spread over 2^-4..1, so a score that left out a
+    # per-row or per-centroid scale would rank differently and fail.
+    rng = np.random.default_rng(41)
+    n, d, c = 1500, 12, 20
+    X = _fp8_exact_rows(rng, n, d, 4)
+    Q = _fp8_exact_rows(rng, 30, d, 2)
+    C = _fp8_exact_rows(rng, c, d, 4)
+    A = oracle.soar_assign(X, C, 1.0, 1)
+    off, ids = oracle.build_ivf(A, c)
+    for t in (3, 7):
+        got_i, got_s = oracle.precision_search(Q, X, C, off, ids, 10, t, rescore)
+        want_i, want_s = oracle.ivf_search(Q, X, C, off, ids, 10, t)
+        np.testing.assert_array_equal(got_i, want_i)
+        np.testing.assert_allclose(got_s, want_s, rtol=1e-12)
+    # the pin has teeth: dropping the per-row scales changes the answer
+    codes, _ = oracle.quantize_rows_fp8(X)
+    unscaled = np.asarray(codes, np.float64) @ np.asarray(Q[0], np.float64)
+    scaled = X.astype(np.float64) @ Q[0].astype(np.float64)
+    assert not np.array_equal(np.argsort(-unscaled, kind="stable")[:10], np.argsort(-scaled, kind="stable")[:10])
+
+
+def test_precision_search_shortlist_is_the_fp8_top_r():
+    # rows that FP8 cannot represent: with rescore = k the answer is the top k
+    # of the FP8 ranking over the probed union (then ordered by exact score),
+    # worked out here from per-row products of the decoded codes
+    X = np.array([[1.0, 0.0], [0.0, 1.0], [0.97, 0.26], [0.9, 0.5], [0.3, 0.95]], dtype=np.float32)
+    Q = np.array([[0.8, 0.6]], dtype=np.float32)
+    C = np.array([[1.0, 0.0], [0.0, 1.0]], dtype=np.float32)
+    A = np.array([[0, 1], [1, 0], [0, 1], [0, 1], [1, 0]])
+    off, ids = oracle.build_ivf(A, 2)
+    q8, qs = oracle.quantize_rows_fp8(Q)
+    x8, xs = oracle.quantize_rows_fp8(X)
+    approx = (x8.astype(np.float64) @ q8[0].astype(np.float64)) * xs * qs[0]
+    top2 = sorted(range(5), key=lambda i: (-approx[i], i))[:2]
+    got_i, _ = oracle.precision_search(Q, X, C, off, ids, 2, 2, 2)
+    exact = X.astype(np.float64) @ Q[0].astype(np.float64)
+    assert sorted(got_i[0].tolist()) == sorted(top2)
+    assert list(got_i[0]) == sorted(top2, key=lambda i: (-exact[i], i))
+
+
+# ------------------------------------------- learned-probe helpers by hand
+
+def test_probe_features_by_hand():
+    Q = np.array([[1.0, 0.0], [0.0, 2.0]])
+    C = np.array([[0.0, 1.0], [2.0, 0.0], [-1.0, 0.5]])
+    # query 0 scores (0, 2, -1) -> descending (2, 0, -1); query 1 scores (2, 0, 1) -> (2, 1, 0)
+    np.testing.assert_array_equal(probe_mlp.features(Q, C, 3), [[1, 0, 2, 0, -1], [0, 2, 2, 1, 0]])
+    np.testing.assert_array_equal(probe_mlp.features(Q, C, 2), [[1, 0, 2, 0], [0, 2, 2, 1]])
+
+
+def test_predict_probes_ceil_and_clamp_by_hand():
+    H = 3
+    p = {"W1": np.zeros((H, 2)), "b1": np.zeros(H), "W2": np.zeros((H, H)), "b2": np.zeros(H),
+         "W3": np.zeros((1, H)), "b3": np.array([np.log(5.2)])}       # y = log 5.2 for every input
+    Z = np.zeros((1, 2))
+    assert probe_mlp.predict_probes(p, Z, 1.0, 100)[0] == 6            # ceil(5.2)
+    assert probe_mlp.predict_probes(p, Z, 0.1, 100)[0] == 1            # ceil(0.52)
+    assert probe_mlp.predict_probes(p, Z, 0.01, 100)[0] == 1           # ceil(0.052)
+    assert probe_mlp.predict_probes(p, Z, 10.0, 20)[0] == 20           # 52 clamped to c
+    # the hidden layers feed through: a ReLU unit with input 1 and weight 1
+    p["W1"][0, 0], p["W2"][0, 0], p["W3"][0, 0], p["b3"][0] = 1.0, 1.0, np.log(3.0), 0.0
+    # y = log(3) * relu(relu(z0)) -> exp(y) = 3^z0: 3^1.5 = 5.196 -> 6; z0 < 0 -> y = 0 -> 1
+    assert probe_mlp.predict_probes(p, np.array([[1.5, 0.0]]), 1.0, 100)[0] == 6
+    assert probe_mlp.predict_probes(p, np.array([[-4.0, 7.0]]), 1.0, 100)[0] == 1
+
+
+def test_mlp_adam_three_steps_by_hand():
+    # gradients +1, -1, +1 on a single weight, lr 0.1, beta1 0.9, beta2 0.999:
+    #   m: 0.1, -0.01, 0.091     v: 0.001, 0.001999, 0.002997001
+    #   bias-corrected m: 1, -0.01/0.19, 0.091/0.271; bias-corrected v: 1 each step
+    # so the weight moves by -0.1, +0.1 * 0.0526316, -0.1 * 0.3357934.
+    # Moments restarted at every step would move it by -0.1, +0.1, -0.1.
+    names = probe_mlp.PARAM_NAMES
+    p = {k: np.zeros((1, 1)) if k.startswith("W") else np.zeros(1) for k in names}
+    p["W2"][0, 0] = 1.0
+    m = {k: np.zeros_like(v) for k, v in p.items()}
+    v = {k: np.zeros_like(x) for k, x in p.items()}
+    want = [0.9, 0.9 + 0.1 * 0.01 / 0.19, 0.9 + 0.1 * 0.01 / 0.19 - 0.1 * 0.091 / 0.271]
+    for step, (g, w) in enumerate(zip((1.0, -1.0, 1.0), want), start=1):
+        grads = {k: np.full_like(x, g) for k, x in p.items()}
+        probe_mlp.adam_step(p, grads, m, v, step, 0.1, eps=0.0)
+        assert p["W2"][0, 0] == pytest.approx(w, rel=1e-12)
+        assert p["b1"][0] == pytest.approx(w - 1.0, rel=1e-12)
+    assert m["W2"][0, 0] == pytest.approx(0.091, rel=1e-12)
+    assert v["W2"][0, 0] == pytest.approx(0.002997001, rel=1e-12)
