@@ -34,7 +34,7 @@ __all__ = [
     "primary_assign", "soar_loss", "soar_assign", "kmeans", "kmeans_objective",
     "build_ivf", "select_partitions", "ivf_search", "partition_positions",
     "kmr_curve", "datapoints_searched", "probe_labels", "fp8_e4m3_round",
-    "quantize_rows_fp8", "precision_search", "bf16_round",
+    "quantize_rows_fp8", "select_partitions_fp8", "precision_search", "bf16_round",
 ]
 
 
@@ -448,6 +448,23 @@ def quantize_rows_fp8(R: np.ndarray):
     return codes, scale
 
 
+def select_partitions_fp8(Q, C, t: int):
+    """MIPS_t(q, C) on the scaled FP8 forms of queries and centroids.
+
+    score(q, C_i) = s_q * s_c * sum_j q8_j c8_j (fp64 sum of the decoded
+    codes); ties to the lower id.  Returns (ids int32 [nq, t], scores f64).
+    """
+    q8, qs = quantize_rows_fp8(np.asarray(Q, dtype=np.float32))
+    c8, cs = quantize_rows_fp8(np.asarray(C, dtype=np.float32))
+    Sc = (q8.astype(F64) @ c8.astype(F64).T) * qs[:, None].astype(F64) * cs[None, :].astype(F64)
+    nq = Sc.shape[0]
+    ids = np.empty((nq, t), dtype=np.int32)
+    sc = np.empty((nq, t), dtype=F64)
+    for i in range(nq):
+        ids[i], sc[i] = topk_desc(Sc[i], t)
+    return ids, sc
+
+
 def precision_search(Q, X, C, offsets, ids, k: int, t: int, rescore: int):
     """Low-precision IVF search followed by exact rescoring.
 
@@ -460,13 +477,12 @@ def precision_search(Q, X, C, offsets, ids, k: int, t: int, rescore: int):
     """
     Qf = np.asarray(Q, dtype=np.float32)
     q8, qs = quantize_rows_fp8(Qf)
-    c8, cs = quantize_rows_fp8(np.asarray(C, dtype=np.float32))
-    Sc = (q8.astype(F64) @ c8.astype(F64).T) * qs[:, None].astype(F64) * cs[None, :].astype(F64)
+    top, _ = select_partitions_fp8(Qf, C, t)
     nq = Qf.shape[0]
     out_i = np.empty((nq, k), dtype=np.int64)
     out_s = np.empty((nq, k), dtype=F64)
     for i in range(nq):
-        parts, _ = topk_desc(Sc[i], t)
+        parts = top[i]
         mem = np.unique(np.concatenate([ids[offsets[p]:offsets[p + 1]] for p in parts])).astype(np.int64)
         x8, xs = quantize_rows_fp8(np.asarray(X[mem], dtype=np.float32))
         approx = (x8.astype(F64) @ q8[i].astype(F64)) * xs.astype(F64) * F64(qs[i])
