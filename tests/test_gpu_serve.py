@@ -23,6 +23,8 @@ def served(soar):
     C = oracle.kmeans(X, init, 10)
     A = oracle.soar_assign(X, C, 1.0, 1)
     ix = soar.soar_index_build(torch.from_numpy(X).cuda(), torch.from_numpy(C).cuda(), torch.from_numpy(A).cuda())
+    ix.centroids_host = C
+    ix.ivf_host = oracle.build_ivf(A, C.shape[0])
     yield X, Q, ix
     ix.close()
 
@@ -62,6 +64,31 @@ def test_results_equal_alone_and_in_a_concurrent_mix(soar, served):
     assert st["queries_in_batches"] == len(Q)
     assert st["batches"] < len(Q)                  # requests were batched
     srv.close()
+
+
+def test_served_results_match_the_oracle(soar, served):
+    # each request of a replayed mixed stream against the oracle's search of
+    # that one query with its own k and t over the same index
+    X, Q, ix = served
+    n = 160
+    rng = np.random.default_rng(23)
+    ks = rng.choice([10, 40, 100], size=n).astype(np.int32)
+    ts = rng.integers(1, 17, size=n).astype(np.int32)
+    arrivals = np.sort(rng.uniform(0.0, 0.02, size=n))
+    srv = soar.Server(ix, max_batch=32, streams=3, memory_budget=1 << 28, max_k=100)
+    rids = srv.submit_many(Q[:n], ks, ts, arrival_s=arrivals)
+    ids, sc, _ = srv.wait_many(rids, 100)
+    srv.close()
+    C = ix.centroids_host
+    off, iv = ix.ivf_host
+    Xd, Qd = X.astype(np.float64), Q.astype(np.float64)
+    for i in range(n):
+        k, t = int(ks[i]), int(ts[i])
+        wi, ws = oracle.ivf_search(Q[i:i + 1], X, C, off, iv, k, t)
+        ex = lambda q, v: Xd[np.asarray(v, np.int64)] @ Qd[i]
+        assert topk_mismatches(ids[i:i + 1, :k], wi, ws, ex) == [], i
+        ok = wi[0] >= 0
+        np.testing.assert_allclose(sc[i, :k][ok], ws[0][ok], rtol=1e-5, atol=1e-6)
 
 
 def test_replayed_arrivals_match_alone_results(soar, served):
