@@ -60,6 +60,8 @@ _SIGS = {
     "soar_index_build": ([_P, _I32, _I64, _I32, _P, _I32, _P, _I32, _I32, ct.POINTER(_P), _P], _I32),
     "soar_index_get_info": ([_P, ct.POINTER(IndexInfo)], _I32),
     "soar_index_free": ([_P], _I32),
+    "soar_index_save": ([_P, ct.c_char_p, _P], _I32),
+    "soar_index_load": ([ct.c_char_p, ct.POINTER(_P), _P], _I32),
     "soar_select_partitions": ([_P, _P, _I32, _I64, _I32, _P, _P, _P], _I32),
     "soar_search": ([_P, _P, _I32, _I64, _I32, _I32, _P, _I32, _P, _P, _P], _I32),
     "soar_exact_mips": ([_P, _I32, _I64, _I32, _P, _I32, _I64, _I32, _P, _P, _P], _I32),
@@ -237,6 +239,16 @@ def soar_index_build(X: torch.Tensor, C: torch.Tensor, assign: torch.Tensor, mod
     _check(load().soar_index_build(_dev(X, "X", ndim=2), _dtype(X), n, d, _dev(C, "C", torch.float32, 2), c,
                                    _dev(assign, "assign", torch.int32, 2), spills, mode, ct.byref(h),
                                    _stream(stream)))
+    return Index(h)
+
+
+def soar_index_save(index: Index, path: str, stream=None) -> None:
+    _check(load().soar_index_save(index.handle, os.fsencode(path), _stream(stream)))
+
+
+def soar_index_load(path: str, stream=None) -> Index:
+    h = ct.c_void_p()
+    _check(load().soar_index_load(os.fsencode(path), ct.byref(h), _stream(stream)))
     return Index(h)
 
 

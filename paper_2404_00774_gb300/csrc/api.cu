@@ -231,6 +231,29 @@ soar_status soar_index_free(soar_index* index) {
   });
 }
 
+soar_status soar_index_save(const soar_index* index, const char* path, cudaStream_t stream) {
+  return guarded([&] {
+    SOAR_REQUIRE(index && path, "null pointer");
+    soar::save_index(index->data, path, stream);
+  });
+}
+
+soar_status soar_index_load(const char* path, soar_index** out, cudaStream_t stream) {
+  return guarded([&] {
+    SOAR_REQUIRE(path && out, "null pointer");
+    soar_index* ix = new soar_index;
+    try {
+      soar::load_index(ix->data, path, stream);
+    } catch (...) {
+      cudaStreamSynchronize(stream);
+      soar::free_index(ix->data);
+      delete ix;
+      throw;
+    }
+    *out = ix;
+  });
+}
+
 soar_status soar_select_partitions(const soar_index* index, const void* Q, soar_dtype dtype, int64_t nq, int32_t t,
                                    int32_t* top_out, float* score_out, cudaStream_t stream) {
   return guarded([&] {

@@ -78,3 +78,17 @@ def test_invalid_arguments_rejected_on_host(lib):
                   ct.c_int32, ct.c_void_p, ct.c_void_p, ct.c_void_p]
     s.restype = ct.c_int32
     assert s(None, dummy, 0, 1, 10, 4, None, 0, dummy, dummy, None) == 1
+
+
+def test_index_load_rejects_a_foreign_file_before_any_device_work(lib, tmp_path):
+    # the header is checked on the host: no GPU is needed to reject the file
+    bad = tmp_path / "not_an_index.bin"
+    bad.write_bytes(b"definitely not a SOAR index file" * 4)
+    lib.soar_index_load.argtypes = [ct.c_char_p, ct.POINTER(ct.c_void_p), ct.c_void_p]
+    lib.soar_index_load.restype = ct.c_int
+    lib.soar_last_error.restype = ct.c_char_p
+    out = ct.c_void_p()
+    assert lib.soar_index_load(str(bad).encode(), ct.byref(out), None) == 1      # SOAR_EINVAL
+    assert b"not a SOAR index" in lib.soar_last_error()
+    assert lib.soar_index_load(str(tmp_path / "missing.bin").encode(), ct.byref(out), None) == 1
+    assert out.value is None
