@@ -1,6 +1,7 @@
 // Exact finishing of the tensor-core partition scan (scan_tc.cu): the
 // screened candidate lists of every (query, partition) pair are rescored
-// exactly in fp32 from the row-major copy of the index, the partitions
+// exactly in fp32 (fp32 rows, or bf16 rows widened exactly) from the
+// row-major copy of the index, the partitions
 // whose lists overflowed are rescanned exactly, spilled copies of a point
 // are dropped (Section 3.5: a spilled point's copies carry bit-identical
 // exact scores) and each query keeps its top k (Section 2.2).
@@ -28,8 +29,8 @@ __global__ void query_bounds(const int2* __restrict__ hdr, const int32_t* __rest
   lstar[q] = best;
 }
 
-// Exact fp32 <q, x> of row-major row `pos` (row stride rs, a multiple of 4;
-// k ascending, the same order for every copy of a point).
+// Exact fp32 <q, x> of row-major row `pos` (row stride rs; k ascending, the
+// same order for every copy of a point).  fp32 rows: rs a multiple of 4.
 __device__ __forceinline__ float exact_dot_rm(const float* __restrict__ q, const float* __restrict__ vec, int rs,
                                               int64_t pos) {
   const float* x = vec + pos * (int64_t)rs;
@@ -46,6 +47,28 @@ __device__ __forceinline__ float exact_dot_rm(const float* __restrict__ q, const
   return acc;
 }
 
+// bf16 rows (rs a multiple of 8): each element widened to fp32 exactly.
+__device__ __forceinline__ float exact_dot_rm(const float* __restrict__ q, const __nv_bfloat16* __restrict__ vec,
+                                              int rs, int64_t pos) {
+  const __nv_bfloat16* x = vec + pos * (int64_t)rs;
+  float acc = 0.f;
+#pragma unroll 4
+  for (int k8 = 0; k8 < rs / 8; ++k8) {
+    const uint4 w = __ldg(reinterpret_cast<const uint4*>(x + 8 * k8));
+    const float4 a0 = __ldg(reinterpret_cast<const float4*>(q + 8 * k8));
+    const float4 a1 = __ldg(reinterpret_cast<const float4*>(q + 8 * k8 + 4));
+    acc = fmaf(a0.x, __uint_as_float(w.x << 16), acc);
+    acc = fmaf(a0.y, __uint_as_float(w.x & 0xffff0000u), acc);
+    acc = fmaf(a0.z, __uint_as_float(w.y << 16), acc);
+    acc = fmaf(a0.w, __uint_as_float(w.y & 0xffff0000u), acc);
+    acc = fmaf(a1.x, __uint_as_float(w.z << 16), acc);
+    acc = fmaf(a1.y, __uint_as_float(w.z & 0xffff0000u), acc);
+    acc = fmaf(a1.z, __uint_as_float(w.w << 16), acc);
+    acc = fmaf(a1.w, __uint_as_float(w.w & 0xffff0000u), acc);
+  }
+  return acc;
+}
+
 
 // Rescoring for 32 < k <= 128 (heap mode, lists of kc <= 256 entries), a
 // warp per (query, partition) slot: the candidates whose upper bound reaches
@@ -53,10 +76,11 @@ __device__ __forceinline__ float exact_dot_rm(const float* __restrict__ q, const
 // a slot whose list overflowed is rescanned exactly over its partition into
 // a shared-memory top-k list.  The slot is rewritten best first and closed
 // by a (-inf, -1) entry when shorter than kc.
+template <typename RowT>
 __global__ void __launch_bounds__(256) rescore_wide(Cand* __restrict__ cand, const int2* __restrict__ hdr, int64_t P,
                                                     const int32_t* __restrict__ pair_vals, int t,
                                                     const float* __restrict__ lstar, const float* __restrict__ Qf,
-                                                    int kp, const float* __restrict__ rows, int rs,
+                                                    int kp, const RowT* __restrict__ rows, int rs,
                                                     const int32_t* __restrict__ ids,
                                                     const int32_t* __restrict__ part_of_pair,
                                                     const int64_t* __restrict__ gstart,
@@ -176,9 +200,10 @@ __global__ void __launch_bounds__(256) rescore_wide(Cand* __restrict__ cand, con
 // top-k (lane j: j-th best rank key), dropping the second copy of a spilled
 // point (its exact score is bit-identical, so its key is too).  Writes the
 // query's ids / scores, padded with -1 / -inf.
+template <typename RowT>
 __global__ void __launch_bounds__(256) finish_queries(
     const Cand* __restrict__ cand, const int2* __restrict__ hdr, const int32_t* __restrict__ inv, int64_t nq, int t,
-    const int32_t* __restrict__ tpq, const float* __restrict__ Qf, int kp, const float* __restrict__ rows, int rs,
+    const int32_t* __restrict__ tpq, const float* __restrict__ Qf, int kp, const RowT* __restrict__ rows, int rs,
     const int32_t* __restrict__ ids, const int32_t* __restrict__ top, const int64_t* __restrict__ gstart,
     const int64_t* __restrict__ part_off, int k, int kc, int64_t* __restrict__ ids_out,
     float* __restrict__ scores_out) {
@@ -311,10 +336,15 @@ __global__ void pair_partitions(const int32_t* __restrict__ top, const int32_t* 
 void finish_tc_queries(const IndexData& ix, const Cand* lists, const int2* hdr, const int32_t* inv, int64_t nq,
                        int t, const int32_t* tpq, const float* Qf, const int32_t* top, int k, int kc,
                        int64_t* ids_out, float* scores_out, cudaStream_t s) {
-  finish_queries<<<ceil_div(nq * 32, 256), 256, 0, s>>>(lists, hdr, inv, nq, t, tpq, Qf, ix.tc_kp,
-                                                        static_cast<const float*>(ix.vectors), ix.row_stride,
-                                                        ix.ids, top, ix.tc_gstart, ix.offsets, k, kc, ids_out,
-                                                        scores_out);
+  if (ix.dtype == SOAR_F32)
+    finish_queries<float><<<ceil_div(nq * 32, 256), 256, 0, s>>>(lists, hdr, inv, nq, t, tpq, Qf, ix.tc_kp,
+                                                                 static_cast<const float*>(ix.vectors), ix.row_stride,
+                                                                 ix.ids, top, ix.tc_gstart, ix.offsets, k, kc,
+                                                                 ids_out, scores_out);
+  else
+    finish_queries<__nv_bfloat16><<<ceil_div(nq * 32, 256), 256, 0, s>>>(
+        lists, hdr, inv, nq, t, tpq, Qf, ix.tc_kp, static_cast<const __nv_bfloat16*>(ix.vectors), ix.row_stride,
+        ix.ids, top, ix.tc_gstart, ix.offsets, k, kc, ids_out, scores_out);
   SOAR_LAUNCHED();
 }
 
@@ -328,9 +358,14 @@ void rescore_tc_wide(const IndexData& ix, Cand* lists, const int2* hdr, const in
   int32_t* part = scr.get<int32_t>(P);
   pair_partitions<<<ceil_div(P, 256), 256, 0, s>>>(top, pair_vals, P, part);
   SOAR_LAUNCHED();
-  rescore_wide<<<ceil_div(P * 32, 256), 256, 0, s>>>(lists, hdr, P, pair_vals, t, lstar, Qf, ix.tc_kp,
-                                                     static_cast<const float*>(ix.vectors), ix.row_stride, ix.ids,
-                                                     part, ix.tc_gstart, ix.offsets, k, kc, tpq);
+  if (ix.dtype == SOAR_F32)
+    rescore_wide<float><<<ceil_div(P * 32, 256), 256, 0, s>>>(lists, hdr, P, pair_vals, t, lstar, Qf, ix.tc_kp,
+                                                              static_cast<const float*>(ix.vectors), ix.row_stride,
+                                                              ix.ids, part, ix.tc_gstart, ix.offsets, k, kc, tpq);
+  else
+    rescore_wide<__nv_bfloat16><<<ceil_div(P * 32, 256), 256, 0, s>>>(
+        lists, hdr, P, pair_vals, t, lstar, Qf, ix.tc_kp, static_cast<const __nv_bfloat16*>(ix.vectors),
+        ix.row_stride, ix.ids, part, ix.tc_gstart, ix.offsets, k, kc, tpq);
   SOAR_LAUNCHED();
 }
 

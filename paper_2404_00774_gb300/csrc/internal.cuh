@@ -62,9 +62,10 @@ struct IndexData {
   float* cent_code_vals = nullptr;  // [c][code_stride] decoded E4M3 code values (FP8)
   float* cent_scales = nullptr;     // [c] (FP8)
   int32_t code_stride = 0;
-  // fp32 rows for the tensor-core scan: each partition padded to 8-row groups,
-  // groups stored in the K-major core-matrix layout of tc.cuh (K = tc_kp)
-  float* tc_rows = nullptr;       // [tc_groups * 8 * tc_kp]
+  // rows for the tensor-core scan in the stored dtype (fp32 or bf16): each
+  // partition padded to 8-row groups, groups stored in the K-major
+  // core-matrix layout of tc.cuh (K = tc_kp, a multiple of 32 bytes)
+  void* tc_rows = nullptr;        // [tc_groups * 8 * tc_kp] elements of dtype
   int64_t* tc_gstart = nullptr;   // [c + 1] first group of each partition
   int32_t* tc_ids = nullptr;      // [tc_groups * 8] point id (-1 on padding)
   float* tc_norms = nullptr;      // [tc_groups * 8] ||x|| (0 on padding)
@@ -91,6 +92,17 @@ namespace soar {
 void build_index(IndexData& ix, const void* X, soar_dtype dt, const float* C, const int32_t* assign,
                  cudaStream_t s);
 void free_index(IndexData& ix);
+
+// A flat index over fx.n rows (fx.vectors, fx.dtype, fx.row_stride, fx.d and
+// fx.c = ceil(n / chunk) set by the caller; chunk a multiple of 8): chunk p
+// holds rows [p * chunk, (p + 1) * chunk) with their ids, plus the
+// tensor-core layout of the rows; every array is taken from `scr`.  Lets the
+// partition scan serve as an exact brute force.
+void build_flat_tc(IndexData& fx, int64_t chunk, cudaStream_t s, Scratch& scr);
+
+// index_io.cu: the index's device arrays to / from a file (format in index_io.cu).
+void save_index(const IndexData& ix, const char* path, cudaStream_t s);
+void load_index(IndexData& ix, const char* path, cudaStream_t s);
 
 void quantize_fp8(const void* V, soar_dtype dt, int64_t m, int32_t d, uint8_t* codes,
                   int32_t code_stride, float* scales, cudaStream_t s);

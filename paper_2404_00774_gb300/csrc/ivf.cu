@@ -86,11 +86,14 @@ __global__ void group_counts(const int64_t* __restrict__ off, int c, int64_t* __
   cnt[p] = p < c ? (off[p + 1] - off[p] + 7) / 8 : 0;
 }
 
-// Partition p's rows -> 8-row groups in the core-matrix layout: element k of
-// padded row i goes to group gstart[p] + i/8, byte (k/4)*128 + (i%8)*16 + (k%4)*4.
-__global__ void fill_tc_rows(const float* __restrict__ rows, int row_stride, int d, const int64_t* __restrict__ off,
+// Partition p's rows -> 8-row groups in the core-matrix layout (tc.cuh): with
+// E = 16 / sizeof(T) elements per 16-byte row chunk, element k of padded row
+// i goes to group gstart[p] + i/8, element (k/E)*8E + (i%8)*E + k%E.
+template <typename T>
+__global__ void fill_tc_rows(const T* __restrict__ rows, int row_stride, int d, const int64_t* __restrict__ off,
                              const int32_t* __restrict__ ids, const int64_t* __restrict__ gstart, int kp,
-                             float* __restrict__ out, int32_t* __restrict__ out_ids) {
+                             T* __restrict__ out, int32_t* __restrict__ out_ids) {
+  constexpr int E = 16 / (int)sizeof(T);
   const int p = blockIdx.x;
   const int64_t r0 = off[p];
   const int size = (int)(off[p + 1] - r0);
@@ -98,21 +101,23 @@ __global__ void fill_tc_rows(const float* __restrict__ rows, int row_stride, int
   const int padded = (int)(gstart[p + 1] - g0) * 8;
   for (int64_t idx = threadIdx.x; idx < (int64_t)padded * kp; idx += blockDim.x) {
     const int i = (int)(idx / kp), k = (int)(idx % kp);
-    const float v = (i < size && k < d) ? rows[(r0 + i) * row_stride + k] : 0.f;
-    out[(g0 + i / 8) * (int64_t)(8 * kp) + (k / 4) * 32 + (i % 8) * 4 + (k % 4)] = v;
+    const T v = (i < size && k < d) ? rows[(r0 + i) * row_stride + k] : T(0.f);
+    out[(g0 + i / 8) * (int64_t)(8 * kp) + (k / E) * (8 * E) + (i % 8) * E + (k % E)] = v;
   }
   for (int i = threadIdx.x; i < padded; i += blockDim.x) out_ids[g0 * 8 + i] = i < size ? ids[r0 + i] : -1;
 }
 
 // ||x|| of every padded row (warp per row).
-__global__ void tc_row_norms(const float* __restrict__ tc_rows, int64_t nrows_padded, int kp, float* __restrict__ norms) {
+template <typename T>
+__global__ void tc_row_norms(const T* __restrict__ tc_rows, int64_t nrows_padded, int kp, float* __restrict__ norms) {
+  constexpr int E = 16 / (int)sizeof(T);
   const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (r >= nrows_padded) return;
-  const float* g = tc_rows + (r / 8) * (int64_t)(8 * kp) + (r % 8) * 4;
+  const T* g = tc_rows + (r / 8) * (int64_t)(8 * kp) + (r % 8) * E;
   float acc = 0.f;
   for (int k = lane; k < kp; k += 32) {
-    const float v = g[(k / 4) * 32 + (k % 4)];
+    const float v = load_elem(g, (k / E) * (8 * E) + (k % E));
     acc = fmaf(v, v, acc);
   }
   acc = warp_sum(acc);
@@ -136,7 +141,64 @@ __global__ void partition_max_norm(const float* __restrict__ norms, const int64_
   }
 }
 
+__global__ void chunk_offsets(int64_t n, int64_t chunk, int c, int64_t* __restrict__ off,
+                              int64_t* __restrict__ gstart, int32_t* __restrict__ order) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p > c) return;
+  const int64_t r = min(n, (int64_t)p * chunk);
+  off[p] = r;
+  gstart[p] = (int64_t)p * (chunk / 8);     // every chunk but the last is a whole number of groups
+  if (p < c) order[p] = p;
+}
+
+__global__ void iota_i32(int32_t* __restrict__ a, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = (int32_t)i;
+}
+
 }  // namespace
+
+void build_flat_tc(IndexData& fx, int64_t chunk, cudaStream_t s, Scratch& scr) {
+  const int64_t n = fx.n;
+  const int c = fx.c, d = fx.d;
+  const size_t esz = fx.dtype == SOAR_F32 ? 4 : 2;
+  const int kstep = fx.dtype == SOAR_F32 ? 8 : 16;
+  fx.tc_kp = (d + kstep - 1) / kstep * kstep;
+  fx.offsets = scr.get<int64_t>((size_t)c + 1);
+  fx.tc_gstart = scr.get<int64_t>((size_t)c + 1);
+  fx.part_order = scr.get<int32_t>(c);
+  chunk_offsets<<<ceil_div((int64_t)c + 1, 256), 256, 0, s>>>(n, chunk, c, fx.offsets, fx.tc_gstart, fx.part_order);
+  SOAR_LAUNCHED();
+  // the last chunk's group count: its rows rounded up to 8
+  const int64_t groups = (int64_t)(c - 1) * (chunk / 8) + (n - (int64_t)(c - 1) * chunk + 7) / 8;
+  fx.tc_groups = groups;
+  SOAR_CUDA(cudaMemcpyAsync(fx.tc_gstart + c, &groups, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  SOAR_CUDA(cudaStreamSynchronize(s));   // the host value above must not go out of scope before the copy
+  fx.ids = scr.get<int32_t>(n);
+  iota_i32<<<ceil_div(n, 256), 256, 0, s>>>(fx.ids, n);
+  SOAR_LAUNCHED();
+  fx.tc_rows = scr.get<unsigned char>(esz * (size_t)groups * 8 * fx.tc_kp);
+  fx.tc_ids = scr.get<int32_t>((size_t)groups * 8);
+  fx.tc_norms = scr.get<float>((size_t)groups * 8);
+  fx.tc_pmax = scr.get<float>(c);
+  if (fx.dtype == SOAR_F32) {
+    fill_tc_rows<float><<<c, 1024, 0, s>>>(static_cast<const float*>(fx.vectors), fx.row_stride, d, fx.offsets, fx.ids,
+                                          fx.tc_gstart, fx.tc_kp, static_cast<float*>(fx.tc_rows), fx.tc_ids);
+    SOAR_LAUNCHED();
+    tc_row_norms<float><<<ceil_div(groups * 8 * 32, 256), 256, 0, s>>>(static_cast<const float*>(fx.tc_rows),
+                                                                       groups * 8, fx.tc_kp, fx.tc_norms);
+  } else {
+    fill_tc_rows<__nv_bfloat16><<<c, 1024, 0, s>>>(static_cast<const __nv_bfloat16*>(fx.vectors), fx.row_stride, d,
+                                                   fx.offsets, fx.ids, fx.tc_gstart, fx.tc_kp,
+                                                  static_cast<__nv_bfloat16*>(fx.tc_rows), fx.tc_ids);
+    SOAR_LAUNCHED();
+    tc_row_norms<__nv_bfloat16><<<ceil_div(groups * 8 * 32, 256), 256, 0, s>>>(
+        static_cast<const __nv_bfloat16*>(fx.tc_rows), groups * 8, fx.tc_kp, fx.tc_norms);
+  }
+  SOAR_LAUNCHED();
+  partition_max_norm<<<c, 256, 0, s>>>(fx.tc_norms, fx.tc_gstart, fx.tc_pmax);
+  SOAR_LAUNCHED();
+}
 
 void quantize_fp8(const void* V, soar_dtype dt, int64_t m, int32_t d, uint8_t* codes, int32_t code_stride,
                   float* scales, cudaStream_t s) {
@@ -255,9 +317,12 @@ void build_index(IndexData& ix, const void* X, soar_dtype dt, const float* C, co
   if (radix_sort_pairs(sk, ix.part_order, sk2, sv2, c, bits_for(mx + 1), s, scr))
     SOAR_CUDA(cudaMemcpyAsync(ix.part_order, sv2, sizeof(int32_t) * c, cudaMemcpyDeviceToDevice, s));
 
-  // fp32 indices also get the tensor-core layout of the rows
-  if (ix.mode == SOAR_SCORE_F32 && dt == SOAR_F32) {
-    ix.tc_kp = (d + 7) / 8 * 8;
+  // full-vector indices also get the tensor-core layout of the rows (fp32
+  // rows for the tf32 scan, bf16 rows for the bf16 scan; K padded to one
+  // 32-byte MMA step)
+  if (ix.mode == SOAR_SCORE_F32) {
+    const int kstep = dt == SOAR_F32 ? 8 : 16;
+    ix.tc_kp = (d + kstep - 1) / kstep * kstep;
     dev_alloc((void**)&ix.tc_gstart, sizeof(int64_t) * (c + 1));
     group_counts<<<ceil_div((int64_t)c + 1, 256), 256, 0, s>>>(ix.offsets, c, ix.tc_gstart);
     SOAR_LAUNCHED();
@@ -266,13 +331,24 @@ void build_index(IndexData& ix, const void* X, soar_dtype dt, const float* C, co
     SOAR_CUDA(cudaMemcpyAsync(&groups, ix.tc_gstart + c, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     SOAR_CUDA(cudaStreamSynchronize(s));
     ix.tc_groups = groups;
-    dev_alloc((void**)&ix.tc_rows, sizeof(float) * (size_t)groups * 8 * ix.tc_kp);
+    dev_alloc(&ix.tc_rows, esz * (size_t)groups * 8 * ix.tc_kp);
     dev_alloc((void**)&ix.tc_ids, sizeof(int32_t) * (size_t)groups * 8);
     dev_alloc((void**)&ix.tc_norms, sizeof(float) * (size_t)groups * 8);
-    fill_tc_rows<<<c, 256, 0, s>>>(static_cast<const float*>(ix.vectors), ix.row_stride, d, ix.offsets, ix.ids,
-                                   ix.tc_gstart, ix.tc_kp, ix.tc_rows, ix.tc_ids);
-    SOAR_LAUNCHED();
-    tc_row_norms<<<ceil_div(groups * 8 * 32, 256), 256, 0, s>>>(ix.tc_rows, groups * 8, ix.tc_kp, ix.tc_norms);
+    if (dt == SOAR_F32) {
+      fill_tc_rows<float><<<c, 256, 0, s>>>(static_cast<const float*>(ix.vectors), ix.row_stride, d, ix.offsets,
+                                            ix.ids, ix.tc_gstart, ix.tc_kp, static_cast<float*>(ix.tc_rows),
+                                            ix.tc_ids);
+      SOAR_LAUNCHED();
+      tc_row_norms<float><<<ceil_div(groups * 8 * 32, 256), 256, 0, s>>>(static_cast<const float*>(ix.tc_rows),
+                                                                         groups * 8, ix.tc_kp, ix.tc_norms);
+    } else {
+      fill_tc_rows<__nv_bfloat16><<<c, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(ix.vectors), ix.row_stride, d,
+                                                    ix.offsets, ix.ids, ix.tc_gstart, ix.tc_kp,
+                                                    static_cast<__nv_bfloat16*>(ix.tc_rows), ix.tc_ids);
+      SOAR_LAUNCHED();
+      tc_row_norms<__nv_bfloat16><<<ceil_div(groups * 8 * 32, 256), 256, 0, s>>>(
+          static_cast<const __nv_bfloat16*>(ix.tc_rows), groups * 8, ix.tc_kp, ix.tc_norms);
+    }
     SOAR_LAUNCHED();
     dev_alloc((void**)&ix.tc_pmax, sizeof(float) * c);
     partition_max_norm<<<c, 256, 0, s>>>(ix.tc_norms, ix.tc_gstart, ix.tc_pmax);

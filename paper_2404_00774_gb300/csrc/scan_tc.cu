@@ -1,17 +1,21 @@
 // Batched IVF partition scan on the 5th-generation tensor cores (tcgen05).
 //
 // One persistent CTA per SM takes work items (partition p, up to 128 of the
-// queries that probe p).  The item's queries form the A operand (M = 128,
-// fp32 rows in shared memory, K-major core-matrix layout); the partition's
-// rows stream through a 4-stage shared-memory ring as B tiles of 64 rows,
-// copied by cp.async.bulk straight from the index, which stores every
-// partition in that same layout.  Per tile one thread issues K/8
-// tcgen05.mma (kind::tf32) into one of two TMEM accumulators (128 lanes x
-// 64 columns); four epilogue warps read the scores back (lane = query).
+// queries that probe p).  The item's queries form the A operand (M = 128
+// rows in shared memory, K-major core-matrix layout); the partition's rows
+// stream through a 4-stage shared-memory ring as B tiles of 64 rows, copied
+// by cp.async.bulk straight from the index, which stores every partition in
+// that same layout.  Per tile one thread issues one tcgen05.mma per 32 bytes
+// of K (kind::tf32 for an fp32 index, kind::f16 with bf16 operands for a
+// bf16 index) into one of two TMEM accumulators (128 lanes x 64 columns);
+// four epilogue warps read the scores back (lane = query).
 //
 // Screening.  kind::tf32 truncates each fp32 operand to 10 mantissa bits,
 // so a screened score s~ lies within 2^-9 ||q|| ||x|| of the fp32 dot
-// product (fp32 accumulation error is far below that).  Per work item the
+// product (fp32 accumulation error is far below that).  For a bf16 index
+// the rows enter exactly and only the fp32 query is rounded to bf16 (8
+// significant bits, a relative error of at most 2^-9 per element), which
+// gives the same bound.  Per work item the
 // kernel uses one bound delta = 2^-8 ||q|| max_p ||x|| (max over the
 // partition's rows: a factor-2 margin).  Per (query, partition) it keeps
 //   * the k best screened scores; with a_k the k-th of them,
@@ -63,7 +67,7 @@ __host__ __device__ constexpr size_t ext_bytes(int k) {
 
 struct TcParams {
   IvfWork work;
-  const float* rows;       // index rows, core-matrix layout, 8-row groups
+  const void* rows;        // index rows (fp32 or bf16), core-matrix layout, 8-row groups
   const int64_t* gstart;   // [c + 1] first 8-row group of each partition
   const float* pmax;       // [c] largest ||x|| of each partition
   const float* Qf;         // [nq][kp] fp32 query rows
@@ -113,18 +117,20 @@ __device__ ItemDesc describe_item(const TcParams& P, int item, int total) {
 // KMAX > 0: register top-k of up to KMAX entries (EXACT: k == KMAX known at
 // compile time, which makes every top-k insertion a fixed compare-exchange
 // chain); KMAX == 0: heap mode.
-template <int KMAX, bool EXACT>
+template <typename ET, int KMAX, bool EXACT>
 __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
+  constexpr uint32_t es = sizeof(ET);            // bytes per operand element
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte aligned carve-up of the dynamic shared memory
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int kp = P.kp, k = EXACT ? KMAX : P.k, S = P.stages;
-  const uint32_t sbo = (uint32_t)kp * 32u;            // bytes between 8-row groups
-  const uint32_t a_bytes = (uint32_t)kM * kp * 4u;
-  const uint32_t b_bytes = (uint32_t)kN * kp * 4u;
-  float* sA = reinterpret_cast<float*>(base);
-  float* sB = reinterpret_cast<float*>(base + a_bytes);
+  const uint32_t sbo = (uint32_t)kp * 8u * es;        // bytes between 8-row groups
+  const uint32_t a_bytes = (uint32_t)kM * kp * es;
+  const uint32_t b_bytes = (uint32_t)kN * kp * es;
+  const char* rows = static_cast<const char*>(P.rows);
+  unsigned char* sA = base;
+  unsigned char* sB = base + a_bytes;
   float* av_s = reinterpret_cast<float*>(base + a_bytes + (size_t)S * b_bytes);  // [kN][kM] parked scores
   // per-slot arrays are interleaved slot-fastest ([entry][kM]) so that the 32
   // lanes of a warp always touch 32 distinct banks
@@ -160,7 +166,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = tmem_base_s;
-  const uint32_t idesc = tc::idesc_tf32(kM, kN);
+  const uint32_t idesc = es == 4 ? tc::idesc_tf32(kM, kN) : tc::idesc_bf16(kM, kN);
   volatile int* abort_v = &abort_s;
   auto give_up = [&]() {
     if (atomicExch(&abort_s, 1) == 0) atomicExch(P.err, 1);
@@ -205,17 +211,35 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
     unsigned gb_pre = 0u;
     float qn_pre = 0.f, pmax_pre = 0.f;
     if (warp >= 3) {
-      float* arow = sA + (m >> 3) * (kp * 8) + (m & 7) * 4;
+      // row m's 16-byte chunk c sits at (m / 8) * 8 K es + c * 128 + (m % 8) * 16
+      unsigned char* arow = sA + (m >> 3) * (kp * 8 * es) + (m & 7) * 16;
+      const int chunks = (int)(kp * es / 16);
       pmax_pre = P.pmax[p];
       if (jq < nqi) {
         const int64_t qi = P.work.query(e0 + jq);
         const float* q = P.Qf + qi * (int64_t)kp;
-        for (int k4 = 0; k4 < kp / 4; ++k4) tc::cp_async16(tc::smem_u32(arow + k4 * 32), q + 4 * k4);
+        if constexpr (es == 4) {
+          for (int c = 0; c < chunks; ++c) tc::cp_async16(tc::smem_u32(arow + c * 128), q + 4 * c);
+        } else {
+          // bf16 operands: the fp32 query rounded to nearest bf16, 8 per chunk
+          for (int c = 0; c < chunks; ++c) {
+            const float4 a0 = __ldg(reinterpret_cast<const float4*>(q + 8 * c));
+            const float4 a1 = __ldg(reinterpret_cast<const float4*>(q + 8 * c + 4));
+            const __nv_bfloat162 b0 = __floats2bfloat162_rn(a0.x, a0.y), b1 = __floats2bfloat162_rn(a0.z, a0.w);
+            const __nv_bfloat162 b2 = __floats2bfloat162_rn(a1.x, a1.y), b3 = __floats2bfloat162_rn(a1.z, a1.w);
+            uint4 w;
+            w.x = *reinterpret_cast<const uint32_t*>(&b0);
+            w.y = *reinterpret_cast<const uint32_t*>(&b1);
+            w.z = *reinterpret_cast<const uint32_t*>(&b2);
+            w.w = *reinterpret_cast<const uint32_t*>(&b3);
+            *reinterpret_cast<uint4*>(arow + c * 128) = w;
+          }
+        }
         qid_pre = qi;
         qn_pre = P.qnorm[qi];
         gb_pre = __ldcg(P.gbound + qi);
       } else {
-        for (int k4 = 0; k4 < kp / 4; ++k4) *reinterpret_cast<float4*>(arow + k4 * 32) = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int c = 0; c < chunks; ++c) *reinterpret_cast<uint4*>(arow + c * 128) = make_uint4(0u, 0u, 0u, 0u);
       }
       tc::cp_async_wait_all();
       tc::fence_async_smem();
@@ -226,23 +250,23 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
       // ---- producer: one thread streams the partition's tiles, keeping the
       // tiles S ahead of the copies in flight prefetched into L2
       if (lane == 0) {
-        auto tile_bytes = [&](int ngr, int t) { return (uint32_t)min(8, ngr - 8 * t) * 8u * kp * 4u; };
-        for (int i = 0; i < min(S, ntiles); ++i)
-          tc::bulk_prefetch_l2(P.rows + (g0 + 8 * i) * 8 * kp, tile_bytes(ng, i));
+        auto tile_bytes = [&](int ngr, int t) { return (uint32_t)min(8, ngr - 8 * t) * 8u * kp * es; };
+        auto group_ptr = [&](int64_t g) { return rows + g * 8 * kp * es; };
+        for (int i = 0; i < min(S, ntiles); ++i) tc::bulk_prefetch_l2(group_ptr(g0 + 8 * i), tile_bytes(ng, i));
         for (int i = 0; i < ntiles; ++i) {
           const uint32_t T = tile_ctr + i, s = T % S, ph = (T / S) & 1;
-          if (i + S < ntiles) tc::bulk_prefetch_l2(P.rows + (g0 + 8 * (i + S)) * 8 * kp, tile_bytes(ng, i + S));
+          if (i + S < ntiles) tc::bulk_prefetch_l2(group_ptr(g0 + 8 * (i + S)), tile_bytes(ng, i + S));
           if (!tc::bar_wait(empty(s), ph ^ 1, abort_v)) { give_up(); break; }
           const uint32_t bytes = tile_bytes(ng, i);
           tc::bar_arrive_expect_tx(full(s), bytes);
-          tc::bulk_copy_g2s(tc::smem_u32(sB) + s * b_bytes, P.rows + (g0 + 8 * i) * 8 * kp, bytes, full(s));
+          tc::bulk_copy_g2s(tc::smem_u32(sB) + s * b_bytes, group_ptr(g0 + 8 * i), bytes, full(s));
           issued_s = (int)(T + 1);
         }
         // claim the next item, resolve it and warm L2 with its first tiles
         next = describe_item(P, atomicAdd(P.counter, 1), total);
         if (next.p >= 0)
           for (int i = 0; i < min(S, (next.ng + 7) / 8); ++i)
-            tc::bulk_prefetch_l2(P.rows + (next.g0 + 8 * i) * 8 * kp, tile_bytes(next.ng, i));
+            tc::bulk_prefetch_l2(group_ptr(next.g0 + 8 * i), tile_bytes(next.ng, i));
       }
     } else if (warp == 1) {
       // ---- MMA issuer.  It never touches an mbarrier (an mbarrier access
@@ -255,9 +279,12 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
         if (lane == 0) {
           tc::fence_after_sync();
           const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB) + s * b_bytes;
-          for (int j = 0; j < kp / 8; ++j)
-            tc::mma_tf32(tmem + b * kN, tc::smem_desc(a0 + j * 256, 128, sbo), tc::smem_desc(b0 + j * 256, 128, sbo),
-                         idesc, j > 0);
+          const int steps = (int)(kp * es / 32);   // one MMA per 32 bytes of K (2 core matrices)
+          for (int j = 0; j < steps; ++j) {
+            const uint64_t ad = tc::smem_desc(a0 + j * 256, 128, sbo), bd = tc::smem_desc(b0 + j * 256, 128, sbo);
+            if constexpr (es == 4) tc::mma_tf32(tmem + b * kN, ad, bd, idesc, j > 0);
+            else tc::mma_bf16(tmem + b * kN, ad, bd, idesc, j > 0);
+          }
           tc::mma_commit(empty(s));                  // the stage is free once these MMAs completed
           tc::mma_commit(tfull(b));
         }
@@ -505,15 +532,25 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
   if (warp == 1) tc::tmem_dealloc(tmem, 2 * kN);
 }
 
-size_t smem_bytes(int kp, int k, int stages) {
-  return 1024 + (size_t)kM * kp * 4 + (size_t)stages * kN * kp * 4 + (size_t)kN * kM * 4 + ext_bytes(k) +
+size_t smem_bytes(int kp, int k, int stages, int es) {
+  return 1024 + (size_t)kM * kp * es + (size_t)stages * kN * kp * es + (size_t)kN * kM * 4 + ext_bytes(k) +
          (size_t)(2 * stages + 4) * 8;
 }
 
-int pick_stages(int kp, int k) {
+int pick_stages(int kp, int k, int es) {
   for (int s = kMaxStages; s >= 2; --s)
-    if (smem_bytes(kp, k, s) <= 227 * 1024 - 1024) return s;   // room for the static shared variables
+    if (smem_bytes(kp, k, s, es) <= 227 * 1024 - 1024) return s;   // room for the static shared variables
   return 0;
+}
+
+template <typename ET>
+void launch_scan_tc(int k, int grid, size_t smem, cudaStream_t s, const TcParams& prm) {
+  auto kern = k == 10   ? scan_tc_kernel<ET, 10, true>
+              : k <= 16 ? scan_tc_kernel<ET, 16, false>
+              : k <= kCand ? scan_tc_kernel<ET, 32, false> : scan_tc_kernel<ET, 0, false>;
+  SOAR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<grid, kThreads, smem, s>>>(prm);
+  SOAR_LAUNCHED();
 }
 
 
@@ -525,8 +562,9 @@ __global__ void fill_u32(unsigned* __restrict__ a, int64_t n, unsigned v) {
 }  // namespace
 
 int scan_tc_max_k(const IndexData& ix) {
+  const int es = ix.dtype == SOAR_F32 ? 4 : 2;
   int k = 0;
-  while (k < kWideK && pick_stages(ix.tc_kp, k + 1) >= 2) ++k;
+  while (k < kWideK && pick_stages(ix.tc_kp, k + 1, es) >= 2) ++k;
   return k;
 }
 
@@ -535,7 +573,8 @@ int scan_tc_list_len(int k) { return list_len_for(k); }
 bool scan_tc_search(const IndexData& ix, const IvfWork& work, int max_items, const float* Qf, const float* qnorm,
                     const int32_t* top, const int32_t* inv, const int32_t* tpq, int64_t nq, int t, int k,
                     Cand* lists, int* err, int64_t* ids_out, float* scores_out, cudaStream_t s, Scratch& scr) {
-  const int stages = pick_stages(ix.tc_kp, k);
+  const int es = ix.dtype == SOAR_F32 ? 4 : 2;
+  const int stages = pick_stages(ix.tc_kp, k, es);
   if (stages < 2 || k > kWideK) fail(SOAR_EUNSUPPORTED, "tensor-core scan: k too large");
   const int kc = list_len_for(k);
   const int64_t P = nq * t;
@@ -547,15 +586,11 @@ bool scan_tc_search(const IndexData& ix, const IvfWork& work, int max_items, con
   SOAR_LAUNCHED();
   prm.counter = scr.get<int>(1);
   SOAR_CUDA(cudaMemsetAsync(prm.counter, 0, sizeof(int), s));
-  const size_t smem = smem_bytes(ix.tc_kp, k, stages);
-  auto kern = k == 10   ? scan_tc_kernel<10, true>
-              : k <= 16 ? scan_tc_kernel<16, false>
-              : k <= kCand ? scan_tc_kernel<32, false> : scan_tc_kernel<0, false>;
-  SOAR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const size_t smem = smem_bytes(ix.tc_kp, k, stages, es);
   const int grid = std::max(1, std::min(max_items, num_sms()));
   stage_mark(s, "scan", true);
-  kern<<<grid, kThreads, smem, s>>>(prm);
-  SOAR_LAUNCHED();
+  if (es == 4) launch_scan_tc<float>(k, grid, smem, s, prm);
+  else launch_scan_tc<__nv_bfloat16>(k, grid, smem, s, prm);
   stage_mark(s, "scan", false);
   stage_mark(s, "rescore", true);
   if (k <= kCand) {

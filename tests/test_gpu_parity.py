@@ -457,3 +457,36 @@ def test_search_rejects_bad_t_and_k(soar, tiny_index):
         soar.soar_search(ix, _t(Q), 10, 65)
     with pytest.raises(soar.SoarError):
         soar.soar_search(ix, _t(Q), 0, 4)
+
+
+@pytest.fixture(scope="module")
+def bf16_index(soar):
+    """A bf16 index at d = 100 (K padded to 112 for the bf16 tensor-core
+    scan), 48 partitions probed by 700 queries (several 128-query work items
+    per partition), built from the oracle's codebook over the bf16-rounded
+    data."""
+    mix = synth.Mixture(100, 30, "isotropic", 0.3, param_seed=71)
+    X = oracle.bf16_round(mix.sample(12_000, seed=72))
+    C = oracle.kmeans(X, synth.init_indices(12_000, 48, seed=73), 3)
+    A = oracle.soar_assign(X, C, 1.0, 1)
+    off, ids = oracle.build_ivf(A, C.shape[0])
+    ix = soar.soar_index_build(_t(X, torch.bfloat16), _t(C), _t(A))
+    Q = mix.sample(700, seed=74)
+    yield X, Q, C, off, ids, ix
+    ix.close()
+
+
+@pytest.mark.parametrize("k,t", [(10, 6), (16, 3), (32, 9), (64, 5), (1, 1)])
+def test_bf16_index_tensor_core_scan_matches_oracle(soar, bf16_index, k, t):
+    # exact results over the bf16 rows (each widened to fp32), whatever the
+    # bf16 rounding of the queries inside the screen
+    X, Q, C, off, ids, ix = bf16_index
+    for qd in (torch.float32, torch.bfloat16):
+        Qin = Q if qd == torch.float32 else oracle.bf16_round(Q)
+        gi, gs = soar.soar_search(ix, _t(Qin, qd), k, t)
+        wi, ws = oracle.ivf_search(Qin, X, C, off, ids, k, t)
+        gi, gs = gi.cpu().numpy(), gs.cpu().numpy()
+        ex = _exact(X, Qin)
+        assert topk_mismatches(gi, wi, ws, ex) == [], (k, t, qd)
+        mx, _ = score_errors(gi, gs, ex)
+        assert mx < 1e-5, (mx, k, t)
