@@ -205,6 +205,25 @@ SOAR_API soar_status soar_search(const soar_index* index, const void* Q, soar_dt
                         int64_t* ids_out, float* scores_out, cudaStream_t stream);
 
 /*
+ * Merge of m result lists per query into one top k (the exchange step of a
+ * search whose rows are sharded over several GPUs: every shard searches its
+ * own rows under the same codebook, so it probes the same partitions, and
+ * the per-shard top k lists are merged; Section 3.5's rule that a point
+ * counts once applies across the lists).
+ *   ids, scores  [nq][m][len] int64 / fp32, each list best first, id -1 (score
+ *                -inf) closing a shorter list, as soar_search writes them
+ *   id_offsets   [m] int64 added to the ids of list j (a shard's first global
+ *                row), or NULL for none
+ *   ids_out, scores_out [nq][k]: the k best by score desc, lower id first on
+ *                ties; an entry equal in id and score to the one before it is
+ *                dropped; -1 / -inf padding.
+ * Requires 1 <= m <= 4096, 1 <= len <= 1024, 1 <= k <= 1024, offset ids < 2^31.
+ */
+SOAR_API soar_status soar_merge_topk(const int64_t* ids, const float* scores, int64_t nq, int32_t m, int32_t len,
+                                     const int64_t* id_offsets, int32_t k, int64_t* ids_out, float* scores_out,
+                                     cudaStream_t stream);
+
+/*
  * Exact maximum inner product search MIPS_k(q, X) (Section 2.1) by brute
  * force: fp32 products and sums over every datapoint.
  *   X [n][d] (xdtype), Q [nq][d] (qdtype), ids_out [nq][k] int64, scores_out [nq][k] fp32.

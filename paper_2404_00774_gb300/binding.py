@@ -66,6 +66,7 @@ _SIGS = {
     "soar_search": ([_P, _P, _I32, _I64, _I32, _I32, _P, _I32, _P, _P, _P], _I32),
     "soar_exact_mips": ([_P, _I32, _I64, _I32, _P, _I32, _I64, _I32, _P, _P, _P], _I32),
     "soar_quantize_fp8": ([_P, _I32, _I64, _I32, _P, _I32, _P, _P], _I32),
+    "soar_merge_topk": ([_P, _P, _I64, _I32, _I32, _P, _I32, _P, _P, _P], _I32),
     "soar_select_partitions_static": ([_P, _P, _I32, _I64, _I32, _P, _P, _P], _I32),
     "soar_check_device": ([], _I32),
     "soar_server_create": ([_P, ct.POINTER(ServerConfig), ct.POINTER(_P)], _I32),
@@ -300,6 +301,22 @@ def soar_exact_mips(X: torch.Tensor, Q: torch.Tensor, k: int, stream=None):
     _check(load().soar_exact_mips(_dev(X, "X", ndim=2), _dtype(X), n, d, _dev(Q, "Q", ndim=2), _dtype(Q), nq, k,
                                   _dev(ids, "ids"), _dev(sc, "scores"), _stream(stream)))
     return ids, sc
+
+
+def soar_merge_topk(ids: torch.Tensor, scores: torch.Tensor, k: int, id_offsets: torch.Tensor | None = None,
+                    stream=None):
+    """ids / scores [nq][m][len] (m lists per query, best first) -> the merged top k [nq][k]."""
+    nq, m, ln = ids.shape
+    if tuple(scores.shape) != (nq, m, ln):
+        raise ValueError("ids and scores must have the same shape")
+    if id_offsets is not None and tuple(id_offsets.shape) != (m,):
+        raise ValueError("id_offsets must have one entry per list")
+    out_i = torch.empty((nq, k), dtype=torch.int64, device=ids.device)
+    out_s = torch.empty((nq, k), dtype=torch.float32, device=ids.device)
+    _check(load().soar_merge_topk(_dev(ids, "ids", torch.int64, 3), _dev(scores, "scores", torch.float32, 3), nq, m,
+                                  ln, _dev(id_offsets, "id_offsets", torch.int64, 1) if id_offsets is not None
+                                  else None, k, _dev(out_i, "ids_out"), _dev(out_s, "scores_out"), _stream(stream)))
+    return out_i, out_s
 
 
 def soar_quantize_fp8(V: torch.Tensor, code_stride: int | None = None, stream=None):

@@ -282,6 +282,18 @@ soar_status soar_search(const soar_index* index, const void* Q, soar_dtype dtype
   });
 }
 
+soar_status soar_merge_topk(const int64_t* ids, const float* scores, int64_t nq, int32_t m, int32_t len,
+                            const int64_t* id_offsets, int32_t k, int64_t* ids_out, float* scores_out,
+                            cudaStream_t stream) {
+  return guarded([&] {
+    SOAR_REQUIRE(ids && scores && ids_out && scores_out, "null pointer");
+    SOAR_REQUIRE(nq >= 1 && m >= 1 && m <= 4096 && len >= 1 && len <= 1024 && k >= 1 && k <= 1024, "bad sizes");
+    SOAR_REQUIRE(nq * (int64_t)m * len < (int64_t(1) << 40), "too many list entries");
+    soar::Scratch scr(stream);
+    soar::merge_topk(ids, scores, nq, m, len, id_offsets, k, ids_out, scores_out, stream, scr);
+  });
+}
+
 soar_status soar_exact_mips(const void* X, soar_dtype xdtype, int64_t n, int32_t d, const void* Q, soar_dtype qdtype,
                             int64_t nq, int32_t k, int64_t* ids_out, float* scores_out, cudaStream_t stream) {
   return guarded([&] {

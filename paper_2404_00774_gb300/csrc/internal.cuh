@@ -154,6 +154,9 @@ void search(const IndexData& ix, const void* Q, soar_dtype dt, int64_t nq, int32
             const int32_t* t_per_query, int32_t rescore, int64_t* ids_out, float* scores_out,
             cudaStream_t s, Scratch& scr);
 
+void merge_topk(const int64_t* ids, const float* scores, int64_t nq, int m, int len, const int64_t* id_offsets,
+                int k, int64_t* ids_out, float* scores_out, cudaStream_t s, Scratch& scr);
+
 void exact_mips(const void* X, soar_dtype xdt, int64_t n, int32_t d, const void* Q, soar_dtype qdt,
                 int64_t nq, int32_t k, int64_t* ids_out, float* scores_out, cudaStream_t s,
                 Scratch& scr);

@@ -389,6 +389,13 @@ __global__ void __launch_bounds__(256) topt_warp_kernel(const float* __restrict_
 
 // ------------------------------------------------------------ grouping
 
+// top[q][j] = j: every query probes every partition (the flat index of the
+// brute force).
+__global__ void all_partitions(int32_t* __restrict__ top, int64_t nq, int c) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < nq * c) top[e] = (int32_t)(e % c);
+}
+
 // Counting sort of the (query, probe) pairs by partition: per-partition
 // counts (a probe beyond the query's own t counts in the sentinel bucket c),
 // then a scatter that also records each pair's position (the inverse map).
@@ -1049,6 +1056,31 @@ void search(const IndexData& ix, const void* Q, soar_dtype dt, int64_t nq, int32
   SOAR_LAUNCHED();
 }
 
+namespace {
+// (id + id_offsets[list], score) of every list entry as merge candidates.
+__global__ void pack_lists(const int64_t* __restrict__ ids, const float* __restrict__ scores, int64_t count, int m,
+                           int len, const int64_t* __restrict__ id_offsets, Cand* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const int64_t id = ids[i];
+  const int list = (int)((i / len) % m);
+  out[i] = id < 0 ? Cand{-INFINITY, -1} : Cand{scores[i], (int32_t)(id + (id_offsets ? id_offsets[list] : 0))};
+}
+}  // namespace
+
+void merge_topk(const int64_t* ids, const float* scores, int64_t nq, int m, int len, const int64_t* id_offsets,
+                int k, int64_t* ids_out, float* scores_out, cudaStream_t s, Scratch& scr) {
+  const int64_t count = nq * m * (int64_t)len;
+  Cand* c = scr.get<Cand>((size_t)count);
+  pack_lists<<<ceil_div(count, 256), 256, 0, s>>>(ids, scores, count, m, len, id_offsets, c);
+  SOAR_LAUNCHED();
+  const int smem = 4 * m * (int)sizeof(uint16_t);
+  SOAR_CUDA(cudaFuncSetAttribute(merge_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  merge_kernel<false><<<ceil_div(nq, 4), 128, smem, s>>>(c, len, nq, 0, nullptr, nullptr, m, k, ids_out, nullptr,
+                                                         scores_out);
+  SOAR_LAUNCHED();
+}
+
 void exact_mips(const void* X, soar_dtype xdt, int64_t n, int32_t d, const void* Q, soar_dtype qdt, int64_t nq,
                 int32_t k, int64_t* ids_out, float* scores_out, cudaStream_t s, Scratch& scr) {
   const size_t esz = xdt == SOAR_F32 ? 4 : 2;
@@ -1061,6 +1093,53 @@ void exact_mips(const void* X, soar_dtype xdt, int64_t n, int32_t d, const void*
     if (stride != d)
       SOAR_CUDA(cudaMemset2DAsync(static_cast<unsigned char*>(pad) + esz * d, esz * stride, 0, esz * (stride - d), n, s));
     rows = pad;
+  }
+  // Tensor-core path: the rows become a flat index of 65 536-row chunks that
+  // every query probes, so the partition scan (tensor-core screening with
+  // exact fp32 finishing) returns the exact top k of all rows.
+  {
+    constexpr int64_t kChunkRows = 65536;
+    IndexData fx;
+    fx.n = n;
+    fx.rows = n;
+    fx.d = d;
+    fx.dtype = xdt;
+    fx.mode = SOAR_SCORE_F32;
+    fx.row_stride = stride;
+    fx.vectors = const_cast<void*>(rows);
+    fx.c = (int)((n + kChunkRows - 1) / kChunkRows);
+    const int kstep = xdt == SOAR_F32 ? 8 : 16;
+    fx.tc_kp = (d + kstep - 1) / kstep * kstep;
+    if (k <= scan_tc_max_k(fx)) {
+      build_flat_tc(fx, kChunkRows, s, scr);
+      const int c = fx.c, len = scan_tc_list_len(k);
+      const size_t qesz = qdt == SOAR_F32 ? 4 : 2;
+      // queries in batches whose candidate lists stay within about 1 GB
+      const int64_t nb = std::max<int64_t>(128, (int64_t(1) << 30) / ((int64_t)c * len * (int64_t)sizeof(Cand)));
+      for (int64_t q0 = 0; q0 < nq; q0 += nb) {
+        const int64_t m = std::min(nb, nq - q0);
+        Scratch bs(s);
+        float* Qf = bs.get<float>((size_t)m * fx.tc_kp);
+        float* qn = bs.get<float>(m);
+        prep_any(static_cast<const char*>(Q) + q0 * d * qesz, qdt, m, d, fx.tc_kp, false, Qf, nullptr, s, qn);
+        int32_t* top = bs.get<int32_t>((size_t)m * c);
+        all_partitions<<<ceil_div(m * c, 256), 256, 0, s>>>(top, m, c);
+        SOAR_LAUNCHED();
+        int32_t* inv = bs.get<int32_t>((size_t)m * c);
+        Cand* lists = bs.get<Cand>((size_t)m * c * len);
+        Grouped g = group_pairs(fx, m, c, nullptr, 128, top, inv, s, bs);
+        IvfWork work{fx.offsets, g.pair_off, g.vals, fx.part_order, g.item_base, c, c, 128};
+        if (!scan_tc_search(fx, work, g.max_items, Qf, qn, top, inv, nullptr, m, c, k, lists, device_error_word(),
+                            ids_out + q0 * k, scores_out + q0 * k, s, bs)) {
+          const int smem = 4 * c * (int)sizeof(uint16_t);
+          SOAR_CUDA(cudaFuncSetAttribute(merge_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+          merge_kernel<true><<<ceil_div(m, 4), 128, smem, s>>>(lists, len, m, c, nullptr, inv, 0, k,
+                                                               ids_out + q0 * k, nullptr, scores_out + q0 * k);
+          SOAR_LAUNCHED();
+        }
+      }
+      return;
+    }
   }
   // float query rows as wide as the expanded data rows
   const int qstride = stride;

@@ -490,3 +490,25 @@ def test_bf16_index_tensor_core_scan_matches_oracle(soar, bf16_index, k, t):
         assert topk_mismatches(gi, wi, ws, ex) == [], (k, t, qd)
         mx, _ = score_errors(gi, gs, ex)
         assert mx < 1e-5, (mx, k, t)
+
+
+@pytest.mark.parametrize("dtype,k", [(torch.float32, 10), (torch.bfloat16, 10), (torch.float32, 64),
+                                     (torch.bfloat16, 33), (torch.float32, 1)])
+def test_exact_mips_several_chunks(soar, dtype, k):
+    # 200 003 rows: three full 65 536-row chunks of the tensor-core brute
+    # force and a ragged fourth; 300 queries (a ragged 128-query work item)
+    rng = np.random.default_rng(81)
+    X = rng.standard_normal((200_003, 24)).astype(np.float32)
+    X /= np.linalg.norm(X, axis=1, keepdims=True)
+    X[150_000:150_040] = X[7]            # exact ties across chunks: lower ids first
+    Q = rng.standard_normal((300, 24)).astype(np.float32)
+    Q[:3] = X[7]
+    Xr = X if dtype == torch.float32 else oracle.bf16_round(X)
+    gi, gs = soar.soar_exact_mips(_t(X, dtype), _t(Q), k)
+    wi, ws = oracle.mips_topk(Q, Xr, k)
+    gi, gs = gi.cpu().numpy(), gs.cpu().numpy()
+    ex = _exact(Xr, Q)
+    assert topk_mismatches(gi, wi, ws, ex) == []
+    mx, _ = score_errors(gi, gs, ex)
+    assert mx < 1e-5
+    np.testing.assert_array_equal(gi[:3, :min(k, 41)], wi[:3, :min(k, 41)])
