@@ -65,6 +65,8 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=300, help="queries timed on the CPU oracle")
     p.add_argument("--no-extras", action="store_true", help="skip the learned-probe and serving measurements")
+    p.add_argument("--at-size", action="store_true",
+                   help="also run the precision (10^7 points) and serving (10^8 points) workloads at full size")
     p.add_argument("--arms", choices=["all", "main"], default="all",
                    help="all: SOAR at lambda 0.5/1/2, spill without SOAR, no spill; main: the timed arm only")
     return p.parse_args()
@@ -431,6 +433,243 @@ def serving_arm(sb, ix, Q, k, rates=(100_000, 300_000, 1_000_000, 3_000_000), n_
             "arrivals": "Poisson, replayed open-loop by the server", "rates": out}
 
 
+def serving_at_size(sb, dev, rates=(20_000, 50_000, 100_000, 200_000), n_req=20_000, n_queries=2000,
+                    train_rows=2_000_000):
+    """The serving workload at its full size: n = 10^8 unit vectors, d = 128,
+    bf16 storage, drawn on the device from a 4 000-component mixture;
+    c = 40 000 partitions (10 Lloyd iterations on the first 2 000 000 draws);
+    SOAR lambda = 1 with one spill.  Requests with k in {10, 100} and t in
+    [32, 512] arrive as a Poisson process at each offered rate and are
+    replayed open-loop into the continuous-batching server (batches of up to
+    1 024 requests, admitted by an HBM budget); p50 / p99 latency from arrival,
+    completed throughput and recall@10 of the served results against exact
+    ground truth over all 10^8 points."""
+    import torch
+    w = synth.WORKLOADS["serving"]
+    mix = synth.mixture_for(w)
+    t0 = time.perf_counter()
+    X = synth.sample_on_device(mix, w.n, w.data_seed, dev, torch.bfloat16)
+    Q = synth.sample_on_device(mix, n_queries, w.query_seed, dev, torch.float32)
+    init = torch.from_numpy(synth.init_indices(train_rows, w.c, w.init_seed)).to(dev)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+
+    def timed_s(fn):
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return out, time.perf_counter() - a
+
+    C, km_s = timed_s(lambda: sb.soar_train_centroids(X[:train_rows], w.c, w.kmeans_iters, init))
+    A, asg_s = timed_s(lambda: sb.soar_assign(X, C, w.lam, w.spills))
+    ix, build_s = timed_s(lambda: sb.soar_index_build(X, C, A))
+    del A
+    truth, gt_s = timed_s(lambda: sb.soar_exact_mips(X, Q, 10)[0])
+    del X
+    torch.cuda.empty_cache()
+    kk, tt = synth.request_mix(n_req, seed=505, ks=(10, 100), t_lo=32, t_hi=512)
+    Qh = Q.cpu().numpy()
+    which = np.arange(n_req) % n_queries
+    truth_h = truth.cpu().numpy()
+    # one full batch of 1 024 requests through soar_search (per-request t,
+    # the batch's largest k): the device time that bounds the throughput
+    tb = torch.from_numpy(tt[:1024].copy()).to(dev)
+    for _ in range(2):
+        sb.soar_search(ix, Q[:1024], int(kk[:1024].max()), int(tt[:1024].max()), t_per_query=tb)
+    _, batch_s = timed_s(lambda: sb.soar_search(ix, Q[:1024], int(kk[:1024].max()), int(tt[:1024].max()),
+                                                t_per_query=tb))
+    out = []
+    for rate in rates:
+        arrivals = synth.poisson_arrivals(rate, n_req, seed=504)
+        srv = sb.Server(ix, max_batch=1024, streams=3, memory_budget=8 << 30, max_k=100)
+        rids = srv.submit_many(Qh[which], kk, tt, arrival_s=arrivals)
+        ids, _, lat = srv.wait_many(rids, 100, timeout_ms=1_200_000)
+        stats = srv.stats()
+        srv.close()
+        hit = (ids[:, :10, None] == truth_h[which][:, None, :]).any(axis=2).sum(axis=1) / 10.0
+        done = arrivals + lat / 1e3
+        out.append({"offered_qps": rate, "achieved_qps": n_req / float(done.max()),
+                    "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                    "recall@10": float(hit.mean()), "batches": stats["batches"],
+                    "mean_batch": stats["queries_in_batches"] / max(1, stats["batches"]),
+                    "max_in_flight": stats["max_in_flight"]})
+        log(f"[bench] serving@{rate}: {out[-1]}")
+    res = {"workload": f"serving: n={w.n} d={w.d} bf16 c={w.c} lambda={w.lam} spills={w.spills}",
+           "requests_per_rate": n_req, "k": [10, 100], "t_range": [32, 512],
+           "arrivals": "Poisson, replayed open-loop by the server", "rates": out,
+           "batch_1024_ms": batch_s * 1e3, "index_bytes": int(ix.info.device_bytes),
+           "setup_s": {"generate": gen_s, "kmeans": km_s, "assign": asg_s, "build": build_s,
+                       "ground_truth": gt_s}}
+    ix.close()
+    return res
+
+
+def size_study(sb, dev, X, Q, k, sizes=(50_000, 200_000, 600_000, 1_183_514), per_partition=400,
+               targets=(0.8, 0.9, 0.95)):
+    """Section 5.3's dataset-size effect on the Glove-shaped data: for nested
+    samples of n rows (the first n of the seeded stream) with c = n / 400
+    partitions (10 Lloyd iterations), the datapoints a no-spill index and a
+    SOAR index (lambda = 1, one spill) search to reach each recall@10 target,
+    and their ratio (no spill / SOAR; above 1: SOAR reads fewer points)."""
+    import torch
+    out = []
+    for n in sizes:
+        Xs = X[:n]
+        c = max(8, n // per_partition)
+        init = torch.from_numpy(synth.init_indices(n, c, 211)).to(dev)
+        C = sb.soar_train_centroids(Xs, c, 10, init)
+        truth = sb.soar_exact_mips(Xs, Q, k)[0]
+        row = {"n": n, "c": c}
+        for name, s in (("no_spill", 0), ("soar", 1)):
+            A = sb.soar_assign(Xs, C, 1.0, s)
+            ix = sb.soar_index_build(Xs, C, A)
+            offsets = ix.offsets()
+            cache = {}
+            for tg in targets:
+                tt, rr = find_t(sb, ix, Q, truth, k, min(c, 1024), tg, cache)
+                dd = float(datapoints_searched(sb, ix, Q, tt, offsets)[0].float().mean()) if tt else None
+                row[f"{name}@{tg}"] = {"t": tt, "recall": rr, "datapoints": dd}
+            ix.close()
+        for tg in targets:
+            a, b = row[f"no_spill@{tg}"]["datapoints"], row[f"soar@{tg}"]["datapoints"]
+            row[f"ratio@{tg}"] = (a / b) if a and b else None
+        out.append(row)
+        log(f"[bench] size study n={n}: {row}")
+    return {"per_partition": per_partition, "lambda": 1.0, "rows": out}
+
+
+def spills_study(sb, X, C, Q, truth, k, max_spills=3, targets=(0.8, 0.9, 0.95)):
+    """Section 3.5.1: more than one spilled assignment (each further spill
+    penalised on every earlier residual direction) and its diminishing
+    returns; datapoints searched at each recall@10 target and index size."""
+    out = []
+    for s in range(0, max_spills + 1):
+        A = sb.soar_assign(X, C, 1.0, s)
+        ix = sb.soar_index_build(X, C, A)
+        offsets = ix.offsets()
+        cache = {}
+        row = {"spills": s, "index_bytes": int(ix.info.device_bytes)}
+        for tg in targets:
+            tt, rr = find_t(sb, ix, Q, truth, k, 512, tg, cache)
+            dd = float(datapoints_searched(sb, ix, Q, tt, offsets)[0].float().mean()) if tt else None
+            row[str(tg)] = {"t": tt, "recall": rr, "datapoints": dd}
+        ix.close()
+        out.append(row)
+        log(f"[bench] spills study: {row}")
+    return {"lambda": 1.0, "rows": out}
+
+
+def precision_at_size(sb, dev, steps, warmup, n_train=1_000_000, n_test=10_000, n_cal=4000, train_rows=1_000_000,
+                      batch=50_000):
+    """The precision workload at its full size (n = 10^7 unit vectors, d = 96,
+    bf16 storage, 1 000-component mixture drawn on the device; c = 10 000
+    partitions by 10 Lloyd iterations on the first 10^6 draws; SOAR lambda =
+    1, one spill) searched exactly on the tensor cores (bf16 rows, exact fp32
+    finishing) at the smallest t reaching recall@10 >= 0.9, and the learned
+    probe count on the same index: 10^6 training queries labelled by the
+    tensor-core brute force, the MLP trained on the GPU, alpha calibrated on
+    4 000 further queries, then evaluated on the 10 000 test queries against
+    fixed-t probing at the same recall target."""
+    import torch
+    from paper_2404_00774_gb300 import probe
+    w = synth.WORKLOADS["precision"]
+    mix = synth.mixture_for(w)
+    t0 = time.perf_counter()
+    X = synth.sample_on_device(mix, w.n, w.data_seed, dev, torch.bfloat16)
+    Q = synth.sample_on_device(mix, n_test, w.query_seed, dev, torch.float32)
+    init = torch.from_numpy(synth.init_indices(train_rows, w.c, w.init_seed)).to(dev)
+    stream = torch.cuda.current_stream()
+
+    def ev_ms(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        out = fn()
+        b.record(stream)
+        b.synchronize()
+        return out, a.elapsed_time(b)
+
+    C, km_ms = ev_ms(lambda: sb.soar_train_centroids(X[:train_rows], w.c, w.kmeans_iters, init))
+    A, asg_ms = ev_ms(lambda: sb.soar_assign(X, C, w.lam, w.spills))
+    ix, build_ms = ev_ms(lambda: sb.soar_index_build(X, C, A))
+    del A
+    truth, gt_ms = ev_ms(lambda: sb.soar_exact_mips(X, Q, w.k)[0])
+    t_fix, rec_fix = find_t(sb, ix, Q, truth, w.k, 512)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    for _ in range(warmup):
+        sb.soar_search(ix, Q, w.k, t_fix)
+    torch.cuda.synchronize()
+    sb.soar_stage_times()
+    sb.soar_stage_timing(True)
+    ts = []
+    for i in range(steps):
+        flush.fill_(float(i))
+        ts.append(ev_ms(lambda: sb.soar_search(ix, Q, w.k, t_fix))[1])
+    sb.soar_stage_timing(False)
+    stages = sb.soar_stage_times()
+    ms_fix = statistics.mean(ts)
+    offsets = ix.offsets()
+    sizes = offsets[1:] - offsets[:-1]
+    top = sb.soar_select_partitions(ix, Q, t_fix).long().reshape(-1)
+    probed = torch.bincount(top, minlength=w.c) > 0
+    scan_ms = stages["scan"][0] / max(1, stages["scan"][1])
+    alg = float(sizes[probed].sum()) * (2 * w.d + 4) + n_test * 4 * w.d + n_test * w.k * 12
+    hbm, _, src = peaks()
+    fixed = {"t": t_fix, "recall": rec_fix, "qps": n_test / (ms_fix / 1e3), "ms_per_step": ms_fix,
+             "datapoints_searched": float(sizes[top.reshape(n_test, t_fix)].sum(dim=1).float().mean()),
+             "stages_ms_per_step": {k2: v[0] / max(1, v[1]) for k2, v in stages.items()},
+             "scan_roofline": {"bound": "hbm", "algorithmic_bytes": alg, "ms": scan_ms,
+                               "achieved_gbs": alg / (scan_ms / 1e3) / 1e9,
+                               "frac": alg / (scan_ms / 1e3) / 1e9 / hbm, "peak_source": f"{src} hbm_gbs",
+                               "rule": "distinct probed partitions x rows x (2d + 4) + queries + results"}}
+    log(f"[bench] precision fixed t: {fixed}")
+    # ---- learned probe count on this index
+    t1 = time.perf_counter()
+    Qtr = synth.sample_on_device(mix, n_train, 304, dev, torch.float32)
+    Qcal = synth.sample_on_device(mix, n_cal, 305, dev, torch.float32)
+    truth_tr = torch.cat([sb.soar_exact_mips(X, Qtr[i:i + batch], w.k)[0] for i in range(0, n_train, batch)])
+    torch.cuda.synchronize()
+    label_gt_s = time.perf_counter() - t1
+    truth_cal = sb.soar_exact_mips(X, Qcal, w.k)[0]
+    Ztr = torch.cat([sb.soar_probe_features(ix, Qtr[i:i + batch], 64) for i in range(0, n_train, batch)])
+    labels = torch.cat([sb.soar_probe_labels(ix, Qtr[i:i + batch], truth_tr[i:i + batch], RECALL_TARGET)
+                        for i in range(0, n_train, batch)])
+    del X
+    params, losses = probe.train(ix, Ztr, labels, hidden=256, steps=3000, batch=4096, lr=1e-3, bf16=True)
+    t_cap = int(torch.quantile(labels.float()[:200_000], 0.99).item())
+    Zcal = sb.soar_probe_features(ix, Qcal, 64)
+    alpha = probe.calibrate_alpha(ix, params, 256, Zcal, Qcal, truth_cal, w.k, t_cap)
+    train_s = time.perf_counter() - t1
+
+    def step():
+        Z = sb.soar_probe_features(ix, Q, 64)
+        tq = sb.soar_mlp_predict_probes(params, Z.shape[1], 256, Z, alpha, t_cap, True)
+        return sb.soar_search(ix, Q, w.k, int(tq.max()), t_per_query=tq), tq
+
+    for _ in range(warmup):
+        step()
+    ts = []
+    for i in range(steps):
+        flush.fill_(float(i))
+        ((ids, _), tq), ms = ev_ms(step)
+        ts.append(ms)
+    rec_l = float((ids[:, :, None] == truth[:, None, :]).any(dim=2).float().mean())
+    ms_l = statistics.mean(ts)
+    learned = {"recall": rec_l, "qps": n_test / (ms_l / 1e3), "ms_per_step": ms_l,
+               "mean_t": float(tq.float().mean()), "max_t": int(tq.max()), "alpha": alpha, "t_cap": t_cap,
+               "train_queries": n_train, "train_steps": 3000, "final_train_loss": losses[-1],
+               "label_mean": float(labels.float().mean()), "label_ground_truth_s": label_gt_s,
+               "setup_s": train_s}
+    log(f"[bench] precision learned probe: {learned}")
+    res = {"workload": f"precision: n={w.n} d={w.d} bf16 c={w.c} lambda={w.lam} spills={w.spills} nq={n_test} k={w.k}",
+           "index": "bf16 rows scanned on the tensor cores (kind::f16), exact fp32 finishing",
+           "fixed_t": fixed, "learned_probe": learned, "index_bytes": int(ix.info.device_bytes),
+           "setup_ms": {"generate_s": time.perf_counter() - t0, "kmeans": km_ms, "assign": asg_ms,
+                        "build": build_ms, "ground_truth": gt_ms}}
+    ix.close()
+    return res
+
+
 # ------------------------------------------------------------------ GPU arm
 
 def run_ours(args):
@@ -609,9 +848,18 @@ def run_ours(args):
         except Exception as e:  # reported, never fatal for the metric
             extras["learned_probe"] = {"error": str(e)[:200]}
         try:
-            extras["serving"] = serving_arm(sb, ix, Q, k)
+            extras["serving_glove"] = serving_arm(sb, ix, Q, k)
         except Exception as e:
-            extras["serving"] = {"error": str(e)[:200]}
+            extras["serving_glove"] = {"error": str(e)[:200]}
+        if world == 1:
+            try:
+                extras["spills_study"] = spills_study(sb, Xd, C, Qd, truth, k)
+            except Exception as e:
+                extras["spills_study"] = {"error": str(e)[:200]}
+            try:
+                extras["size_study"] = size_study(sb, dev, Xd, Qd[:2000], k)
+            except Exception as e:
+                extras["size_study"] = {"error": str(e)[:200]}
 
     # ---- CPU oracle baseline (rank 0 only, N = 1 only)
     cpu = None
@@ -647,10 +895,24 @@ def run_ours(args):
         "stages_ms_per_step": {s: v[0] / max(1, v[1]) for s, v in stages.items()},
         **extras,
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     for ixx, _ in built.values():
         ixx.close()
+    # ---- the precision and serving workloads at their full sizes (10^7 and
+    # 10^8 points; each builds its own index)
+    if args.at_size and world == 1:
+        del Xd, truth
+        torch.cuda.empty_cache()
+        try:
+            line["precision"] = precision_at_size(sb, dev, args.steps, args.warmup)
+        except Exception as e:   # reported, never fatal for the metric
+            line["precision"] = {"error": str(e)[:300]}
+        torch.cuda.empty_cache()
+        try:
+            line["serving"] = serving_at_size(sb, dev)
+        except Exception as e:   # reported, never fatal for the metric
+            line["serving"] = {"error": str(e)[:300]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
     return 0

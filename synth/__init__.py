@@ -108,6 +108,30 @@ class Mixture:
         return out
 
 
+def sample_on_device(mix: Mixture, n: int, seed: int, device, dtype=None, chunk: int = 1 << 22):
+    """``n`` unit-normalised draws of an isotropic mixture made on a CUDA
+    device with torch's counter-based (Philox) generator, for workloads too
+    large to draw on the host (the serving workload's 10^8 points).  Same
+    mixture parameters as ``Mixture.sample``, a different random stream:
+    component uniform over the components, then mean + sigma * N(0, I),
+    normalised in fp32, cast to ``dtype`` (default fp32).  Deterministic for a
+    given seed, device type and chunk size."""
+    import torch
+    if mix.kind != "isotropic":
+        raise ValueError("device sampling covers isotropic mixtures")
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    means = torch.as_tensor(mix.means, dtype=torch.float32, device=device)
+    out = torch.empty((n, mix.d), dtype=dtype or torch.float32, device=device)
+    for lo in range(0, n, chunk):
+        m = min(chunk, n - lo)
+        comp = torch.randint(0, mix.m, (m,), generator=g, device=device)
+        v = means[comp] + mix.sigma * torch.randn((m, mix.d), generator=g, device=device)
+        v /= v.norm(dim=1, keepdim=True)
+        out[lo:lo + m] = v.to(out.dtype)
+    return out
+
+
 def mixture_for(w: Workload) -> Mixture:
     return Mixture(w.d, w.components, w.kind, w.sigma, w.param_seed, w.mean_scale)
 
