@@ -48,7 +48,10 @@ constexpr int kEpi = 256;      // epilogue threads (8 warps: 4 lane quarters x 2
 constexpr int kThr = 96 + kEpi;   // producer, MMA issuer, gate, epilogue
 constexpr int kStagesMax = 8;
 constexpr int kStageBytes = 32768;   // codebook stage: 32 KB keeps bulk copies near full L2 bandwidth
-constexpr int kList = 8;       // candidates kept per point
+constexpr int kList = 16;      // candidates kept per point
+// parking area: a tile's 16 screened bounds per epilogue thread, overlaid at
+// the end by the merge area (two lists of kList plus two scalars per point)
+constexpr int kPark = 16 * kEpi > 2 * kList * kTM + 2 * kTM ? 16 * kEpi : 2 * kList * kTM + 2 * kTM;
 
 // B tile width per pass: both fill the 512 TMEM columns with two buffers.
 __host__ __device__ constexpr int tile_n(int ndir) { return ndir ? 128 : 256; }
@@ -102,7 +105,7 @@ __global__ void __launch_bounds__(kThr, 1) assign_tc_kernel(AsgParams<XT> P) {
   int* mid_s = reinterpret_cast<int*>(mlb_s + kList * kTM);                 // [kList][kTM]
   float* mu_s = reinterpret_cast<float*>(mid_s + kList * kTM);              // [kTM] U of the second half
   float* mev_s = mu_s + kTM;                                                // [kTM]
-  float* nx_s = lb_s + 16 * kEpi;                                           // [kTM] ||x||
+  float* nx_s = lb_s + kPark;                                               // [kTM] ||x||
   float* xr_s = nx_s + kTM;                                                 // [kTM] <x, r_hat>
   float* rn_s = xr_s + kTM;                                                 // [kTM] 1 or 0 (zero residual)
   int* prior_s = reinterpret_cast<int*>(rn_s + kTM);                        // [kTM]
@@ -528,7 +531,7 @@ __global__ void tile_max_norms(const float* __restrict__ n1, int c, int N, int c
 }
 
 // Direct-form decision among the candidates of each queued point (warp per
-// point, persistent over the queue): four lanes per listed candidate, or,
+// point, persistent over the queue): two lanes per listed candidate, or,
 // for a point the screen flagged, the lanes split every centroid not yet
 // assigned to it.  Lower index on equal losses.
 template <typename XT>
@@ -558,13 +561,13 @@ __global__ void refine_list(const XT* __restrict__ X, int d, const float* __rest
     int bi = -1;
     const bool listed = !ovf[p] && cand[p * kList] >= 0;
     if (listed) {
-      static_assert(kList * 4 == 32, "four lanes per candidate");
-      const int g = lane >> 2, part = lane & 3;
+      static_assert(kList * 2 == 32, "two lanes per candidate");
+      const int g = lane >> 1, part = lane & 1;
       const int cq = cand[p * kList + g];
       float dist = 0.f, pr = 0.f;
       if (cq >= 0) {
         const float* cv = C + (int64_t)cq * d;
-        for (int k = part; k < d; k += 4) {
+        for (int k = part; k < d; k += 2) {
           const float xv = load_elem(x, k);
           const float v = xv - cv[k];
           dist = fmaf(v, v, dist);
@@ -572,7 +575,7 @@ __global__ void refine_list(const XT* __restrict__ X, int d, const float* __rest
         }
       }
 #pragma unroll
-      for (int o = 1; o < 4; o <<= 1) {
+      for (int o = 1; o < 2; o <<= 1) {
         dist += __shfl_xor_sync(kFull, dist, o);
         pr += __shfl_xor_sync(kFull, pr, o);
       }
@@ -606,7 +609,7 @@ __global__ void refine_list(const XT* __restrict__ X, int d, const float* __rest
 }
 
 size_t smem_for(int kp, int ndir, int s) {
-  return 128 + (size_t)(1 + ndir) * kTM * kp * 4 + (size_t)s * kStageBytes + (size_t)16 * kEpi * 4 +
+  return 128 + (size_t)(1 + ndir) * kTM * kp * 4 + (size_t)s * kStageBytes + (size_t)kPark * 4 +
          (size_t)4 * kTM * 4 + (size_t)(2 * s + 4) * 8;
 }
 
