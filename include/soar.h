@@ -400,6 +400,16 @@ SOAR_API soar_status soar_check_device(void);
 /* Number of CUDA kernels this library has launched in this process. */
 SOAR_API uint64_t soar_kernel_launches(void);
 
+/* Longest wait, in SM clock cycles, of the partition scan's pipeline (a
+ * copy landing, an accumulator filling or freeing) before the waiting CTA
+ * gives up: it then records the failure for soar_check_device, stops taking
+ * work, lets its copies and MMAs in flight land (those waits keep the default
+ * of about 2^31 cycles) and frees its tensor memory, and the finishing of that
+ * search reads its unwritten lists as empty.  0 restores the default.  Applies
+ * to the scans launched after the call; a test of the failure path, not a
+ * tuning knob. */
+SOAR_API soar_status soar_set_wait_limit(int64_t cycles);
+
 /* Turns on (1) or off (0) CUDA-event timing of the named stages of
  * soar_search ("select", "group", "scan", "merge", "rescore"); events are
  * recorded on the call's stream around each stage, adding no synchronisation. */

@@ -84,6 +84,7 @@ _SIGS = {
     "soar_mlp_adam": ([_P, _P, _P, _P, _I64, _I32, _F32, _F32, _F32, _F32, _P], _I32),
     "soar_mlp_predict_probes": ([_P, _I32, _I32, _P, _I32, _I32, _F32, _I32, _P, _P], _I32),
     "soar_kernel_launches": ([], ct.c_uint64),
+    "soar_set_wait_limit": ([_I64], _I32),
     "soar_stage_timing": ([_I32], _I32),
     "soar_stage_times": ([ct.c_char_p, _I32, _P, _P, _I32], _I32),
 }
@@ -337,6 +338,11 @@ def soar_check_device() -> None:
 def soar_kernel_launches() -> int:
     """Kernels launched by the library so far in this process."""
     return int(load().soar_kernel_launches())
+
+
+def soar_set_wait_limit(cycles: int) -> None:
+    """Longest scan pipeline wait in SM cycles before a CTA gives up (0: default)."""
+    _check(load().soar_set_wait_limit(int(cycles)))
 
 
 def soar_stage_timing(enable: bool) -> None:

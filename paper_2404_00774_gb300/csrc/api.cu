@@ -6,6 +6,7 @@
 #include <mutex>
 
 #include "internal.cuh"
+#include "scan_common.cuh"
 
 namespace soar {
 
@@ -405,6 +406,13 @@ soar_status soar_check_device(void) {
 }
 
 uint64_t soar_kernel_launches(void) { return soar::g_launches.load(); }
+
+soar_status soar_set_wait_limit(int64_t cycles) {
+  return guarded([&] {
+    SOAR_REQUIRE(cycles >= 0, "cycles must be >= 0");
+    soar::set_scan_wait_limit(cycles);
+  });
+}
 
 soar_status soar_stage_timing(int enable) {
   return guarded([&] {

@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(256) rescore_wide(Cand* __restrict__ cand, con
   const int j = pair_vals[e] - (int)(q * t);
   if (tpq && j >= min(max(tpq[q], 1), t)) return;
   const int2 h = hdr[e];
-  const int cnt = h.y & 0x7fffffff;
+  const int cnt = min(h.y & 0x7fffffff, kc);
   const bool ovf = h.y < 0;
   const float bound = lstar[q];
   const float* qv = Qf + q * (int64_t)kp;
@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(256) finish_queries(
       e_l = inv[q * t + j];
       const int hy = hdr[e_l].y;
       ovf_l = hy < 0;
-      cnt_l = ovf_l ? 0 : (hy & 0x7fffffff);
+      cnt_l = ovf_l ? 0 : min(hy & 0x7fffffff, kc);
     }
     int incl = cnt_l;
 #pragma unroll

@@ -78,6 +78,9 @@ bool scan_tc_search(const IndexData& ix, const IvfWork& work, int max_items, con
                     const int32_t* top, const int32_t* inv, const int32_t* tpq, int64_t nq, int t, int k,
                     Cand* lists, int* err, int64_t* ids_out, float* scores_out, cudaStream_t s, Scratch& scr);
 int scan_tc_max_k(const IndexData& ix);
+// SM cycles a pipeline wait of the scan may take before its CTA gives up
+// (0: the default of about a second); the teardown's waits keep the default.
+void set_scan_wait_limit(long long cycles);
 int scan_tc_list_len(int k);
 
 }  // namespace soar

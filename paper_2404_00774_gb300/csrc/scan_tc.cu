@@ -13,9 +13,14 @@
 // Screening.  kind::tf32 truncates each fp32 operand to 10 mantissa bits,
 // so a screened score s~ lies within 2^-9 ||q|| ||x|| of the fp32 dot
 // product (fp32 accumulation error is far below that).  For a bf16 index
-// the rows enter exactly and only the fp32 query is rounded to bf16 (8
-// significant bits, a relative error of at most 2^-9 per element), which
-// gives the same bound.  Per work item the
+// the rows enter exactly and the fp32 query enters as two bf16 terms, q_hi =
+// bf16(q) and q_lo = bf16(q - q_hi), in two MMAs into the same accumulator:
+// the dropped part is below 2^-18 |q_k| per element, and with the fp32
+// accumulation of 2K products and the fp32 rounding of the exact score the
+// screened score lies within (2^-18 + 2.5 K 2^-23) ||q|| ||x|| of it, so the
+// band delta = max(2^-12, 4 (2^-18 + 2.5 K 2^-23)) ||q|| max_p ||x|| (at
+// least a factor 2.9 for K <= 128) is 16 times narrower than the tf32 one;
+// on data with tight clusters that keeps the candidate lists short.  Per work item the
 // kernel uses one bound delta = 2^-8 ||q|| max_p ||x|| (max over the
 // partition's rows: a factor-2 margin).  Per (query, partition) it keeps
 //   * the k best screened scores; with a_k the k-th of them,
@@ -73,9 +78,11 @@ struct TcParams {
   const float* Qf;         // [nq][kp] fp32 query rows
   const float* qnorm;      // [nq]
   int kp;                  // K, a multiple of 8
+  float dscale;            // delta / (||q|| max_p ||x||)
   int k;                   // top-k length
   int kc;                  // candidate-list capacity per pair slot
   int stages;
+  long long wait_limit;    // SM cycles a pipeline wait may take before the CTA gives up
   int* counter;            // work-item counter
   int* err;                // set to 1 when a wait expired
   unsigned* gbound;        // [nq] per-query lower bound of the final k-th best exact score (ordered key)
@@ -126,12 +133,12 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int kp = P.kp, k = EXACT ? KMAX : P.k, S = P.stages;
   const uint32_t sbo = (uint32_t)kp * 8u * es;        // bytes between 8-row groups
-  const uint32_t a_bytes = (uint32_t)kM * kp * es;
+  const uint32_t a_bytes = (uint32_t)kM * kp * es;     // one part (bf16: hi, then lo)
   const uint32_t b_bytes = (uint32_t)kN * kp * es;
   const char* rows = static_cast<const char*>(P.rows);
   unsigned char* sA = base;
-  unsigned char* sB = base + a_bytes;
-  float* av_s = reinterpret_cast<float*>(base + a_bytes + (size_t)S * b_bytes);  // [kN][kM] parked scores
+  unsigned char* sB = base + (es == 4 ? 1 : 2) * a_bytes;
+  float* av_s = reinterpret_cast<float*>(sB + (size_t)S * b_bytes);  // [kN][kM] parked scores
   // per-slot arrays are interleaved slot-fastest ([entry][kM]) so that the 32
   // lanes of a warp always touch 32 distinct banks
   float* ext_s = av_s + kN * kM;   // candidates [kCand][kM] (+ rows) or the heap [k][kM]
@@ -221,25 +228,33 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
         if constexpr (es == 4) {
           for (int c = 0; c < chunks; ++c) tc::cp_async16(tc::smem_u32(arow + c * 128), q + 4 * c);
         } else {
-          // bf16 operands: the fp32 query rounded to nearest bf16, 8 per chunk
+          // bf16 operands: the fp32 query as hi = bf16(q) (first A part) and
+          // lo = bf16(q - hi) (second A part), 8 elements per chunk
           for (int c = 0; c < chunks; ++c) {
             const float4 a0 = __ldg(reinterpret_cast<const float4*>(q + 8 * c));
             const float4 a1 = __ldg(reinterpret_cast<const float4*>(q + 8 * c + 4));
-            const __nv_bfloat162 b0 = __floats2bfloat162_rn(a0.x, a0.y), b1 = __floats2bfloat162_rn(a0.z, a0.w);
-            const __nv_bfloat162 b2 = __floats2bfloat162_rn(a1.x, a1.y), b3 = __floats2bfloat162_rn(a1.z, a1.w);
-            uint4 w;
-            w.x = *reinterpret_cast<const uint32_t*>(&b0);
-            w.y = *reinterpret_cast<const uint32_t*>(&b1);
-            w.z = *reinterpret_cast<const uint32_t*>(&b2);
-            w.w = *reinterpret_cast<const uint32_t*>(&b3);
-            *reinterpret_cast<uint4*>(arow + c * 128) = w;
+            const float v[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            uint32_t hi[4], lo[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+              const __nv_bfloat162 bh = __floats2bfloat162_rn(v[2 * h], v[2 * h + 1]);
+              const float2 fh = __bfloat1622float2(bh);
+              const __nv_bfloat162 bl = __floats2bfloat162_rn(v[2 * h] - fh.x, v[2 * h + 1] - fh.y);
+              hi[h] = *reinterpret_cast<const uint32_t*>(&bh);
+              lo[h] = *reinterpret_cast<const uint32_t*>(&bl);
+            }
+            *reinterpret_cast<uint4*>(arow + c * 128) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            *reinterpret_cast<uint4*>(arow + a_bytes + c * 128) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
           }
         }
         qid_pre = qi;
         qn_pre = P.qnorm[qi];
         gb_pre = __ldcg(P.gbound + qi);
       } else {
-        for (int c = 0; c < chunks; ++c) *reinterpret_cast<uint4*>(arow + c * 128) = make_uint4(0u, 0u, 0u, 0u);
+        for (int c = 0; c < chunks; ++c) {
+          *reinterpret_cast<uint4*>(arow + c * 128) = make_uint4(0u, 0u, 0u, 0u);
+          if (es == 2) *reinterpret_cast<uint4*>(arow + a_bytes + c * 128) = make_uint4(0u, 0u, 0u, 0u);
+        }
       }
       tc::cp_async_wait_all();
       tc::fence_async_smem();
@@ -256,7 +271,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
         for (int i = 0; i < ntiles; ++i) {
           const uint32_t T = tile_ctr + i, s = T % S, ph = (T / S) & 1;
           if (i + S < ntiles) tc::bulk_prefetch_l2(group_ptr(g0 + 8 * (i + S)), tile_bytes(ng, i + S));
-          if (!tc::bar_wait(empty(s), ph ^ 1, abort_v)) { give_up(); break; }
+          if (!tc::bar_wait(empty(s), ph ^ 1, abort_v, P.wait_limit)) { give_up(); break; }
           const uint32_t bytes = tile_bytes(ng, i);
           tc::bar_arrive_expect_tx(full(s), bytes);
           tc::bulk_copy_g2s(tc::smem_u32(sB) + s * b_bytes, group_ptr(g0 + 8 * i), bytes, full(s));
@@ -282,8 +297,12 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
           const int steps = (int)(kp * es / 32);   // one MMA per 32 bytes of K (2 core matrices)
           for (int j = 0; j < steps; ++j) {
             const uint64_t ad = tc::smem_desc(a0 + j * 256, 128, sbo), bd = tc::smem_desc(b0 + j * 256, 128, sbo);
-            if constexpr (es == 4) tc::mma_tf32(tmem + b * kN, ad, bd, idesc, j > 0);
-            else tc::mma_bf16(tmem + b * kN, ad, bd, idesc, j > 0);
+            if constexpr (es == 4) {
+              tc::mma_tf32(tmem + b * kN, ad, bd, idesc, j > 0);
+            } else {
+              tc::mma_bf16(tmem + b * kN, ad, bd, idesc, j > 0);
+              tc::mma_bf16(tmem + b * kN, tc::smem_desc(a0 + a_bytes + j * 256, 128, sbo), bd, idesc, 1);
+            }
           }
           tc::mma_commit(empty(s));                  // the stage is free once these MMAs completed
           tc::mma_commit(tfull(b));
@@ -299,7 +318,8 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
         const uint32_t T = tile_ctr + i, s = T % S, ph = (T / S) & 1, b = T & 1, tph = (T >> 1) & 1;
         int ok = 1;
         if (lane == 0) {
-          ok = tc::bar_wait(full(s), ph, abort_v) && tc::bar_wait(tempty(b), tph ^ 1, abort_v);
+          ok = tc::bar_wait(full(s), ph, abort_v, P.wait_limit) &&
+               tc::bar_wait(tempty(b), tph ^ 1, abort_v, P.wait_limit);
           if (!ok) give_up();
           else consumed_s = (int)(T + 1);
           tc::fence_before_sync();
@@ -310,7 +330,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
     } else {
       // ---- epilogue: screening bounds and candidate rows per query
       const bool active = jq < nqi;
-      const float dlt = ldexpf(qn_pre, -8) * pmax_pre;   // |s~ - exact| < dlt / 2 for every row of p
+      const float dlt = P.dscale * qn_pre * pmax_pre;   // |s~ - exact| < dlt / 2 for every row of p
       // G_q, published by this query's finished partitions, bounds its final
       // k-th best exact score from below: rows with s~ + dlt < G_q cannot count
       const int64_t qid = qid_pre;
@@ -336,7 +356,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
       Cand* glist = P.cand + (e0 + (active ? jq : 0)) * (int64_t)P.kc;     // heap mode candidates
       for (int i = 0; i < ntiles; ++i) {
         const uint32_t T = tile_ctr + i, b = T & 1, tph = (T >> 1) & 1;
-        const bool ok = tc::bar_wait(tfull(b), tph, abort_v);
+        const bool ok = tc::bar_wait(tfull(b), tph, abort_v, P.wait_limit);
         if (!ok) give_up();
         tc::fence_after_sync();
         uint32_t r0[32], r1[32];
@@ -533,8 +553,15 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
 }
 
 size_t smem_bytes(int kp, int k, int stages, int es) {
-  return 1024 + (size_t)kM * kp * es + (size_t)stages * kN * kp * es + (size_t)kN * kM * 4 + ext_bytes(k) +
+  // the A operand takes kM * kp * 4 bytes either way (fp32, or bf16 hi and lo)
+  return 1024 + (size_t)kM * kp * 4 + (size_t)stages * kN * kp * es + (size_t)kN * kM * 4 + ext_bytes(k) +
          (size_t)(2 * stages + 4) * 8;
+}
+
+// delta / (||q|| max_p ||x||) of the screen (see the header comment)
+float delta_scale(int kp, int es) {
+  if (es == 4) return 1.f / 256.f;
+  return std::max(1.f / 4096.f, 4.f * (std::ldexp(1.f, -18) + 2.5f * kp * std::ldexp(1.f, -23)));
 }
 
 int pick_stages(int kp, int k, int es) {
@@ -559,7 +586,19 @@ __global__ void fill_u32(unsigned* __restrict__ a, int64_t n, unsigned v) {
   if (i < n) a[i] = v;
 }
 
+// Every pair slot's header before the scan: bound -inf, no candidates, so
+// that a slot the scan never wrote (a CTA that gave up a wait) is read by the
+// finishing kernels as an empty list.
+__global__ void clear_headers(int2* __restrict__ hdr, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) hdr[i] = make_int2(__float_as_int(-INFINITY), 0);
+}
+
+std::atomic<long long> g_wait_limit{0};
+
 }  // namespace
+
+void set_scan_wait_limit(long long cycles) { g_wait_limit.store(cycles > 0 ? cycles : 0); }
 
 int scan_tc_max_k(const IndexData& ix) {
   const int es = ix.dtype == SOAR_F32 ? 4 : 2;
@@ -579,8 +618,11 @@ bool scan_tc_search(const IndexData& ix, const IvfWork& work, int max_items, con
   const int kc = list_len_for(k);
   const int64_t P = nq * t;
   int2* hdr = scr.get<int2>(P);
-  TcParams prm{work, ix.tc_rows, ix.tc_gstart, ix.tc_pmax, Qf, qnorm, ix.tc_kp, k, kc, stages,
-               nullptr, err, nullptr, lists, hdr};
+  clear_headers<<<ceil_div(P, 256), 256, 0, s>>>(hdr, P);
+  SOAR_LAUNCHED();
+  const long long lim = g_wait_limit.load();
+  TcParams prm{work, ix.tc_rows, ix.tc_gstart, ix.tc_pmax, Qf, qnorm, ix.tc_kp, delta_scale(ix.tc_kp, es), k, kc,
+               stages, lim > 0 ? lim : tc::kWaitLimit, nullptr, err, nullptr, lists, hdr};
   prm.gbound = scr.get<unsigned>(nq);
   fill_u32<<<ceil_div(nq, 256), 256, 0, s>>>(prm.gbound, nq, 0x007fffffu);   // ordered key of -inf
   SOAR_LAUNCHED();

@@ -56,14 +56,16 @@ __device__ __forceinline__ bool bar_try_wait_sleep(uint32_t bar, uint32_t parity
   return ok != 0;
 }
 
-// Waits for the phase of `parity` to complete, at most ~2^31 SM cycles (about
-// a second); gives up early when *abort becomes non-zero.  Returns false when
-// it gave up.
-__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
+// Waits for the phase of `parity` to complete, at most `limit` SM cycles
+// (by default 2^31, about a second); gives up early when *abort becomes
+// non-zero.  Returns false when it gave up.
+constexpr long long kWaitLimit = 1ll << 31;
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, volatile int* abort,
+                                         long long limit = kWaitLimit) {
   const long long t0 = clock64();
   while (!bar_try_wait(bar, parity)) {
     if (*abort) return false;
-    if (clock64() - t0 > (1ll << 31)) return false;
+    if (clock64() - t0 > limit) return false;
   }
   return true;
 }

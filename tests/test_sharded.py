@@ -92,7 +92,7 @@ def test_shard_bounds_cover_the_rows():
 
 def test_two_gloo_ranks_equal_the_unsharded_search():
     world, port = 2, _free_port()
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         mp.spawn(_rank_main, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
