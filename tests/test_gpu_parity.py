@@ -444,8 +444,20 @@ def test_fp8_index_search_with_rescoring(soar, tiny):
     wi, ws = oracle.precision_search(Qb, Xb, C, off, ids, 10, 4, 200)
     gi = gi.cpu().numpy()
     bad = topk_mismatches(gi, wi, ws, _exact(Xb, Qb))
-    # a query may differ only when its FP8 shortlist boundary is a near-tie
-    assert len(bad) <= 2, bad
+    # a query may differ only where the oracle's own decision is a near-tie
+    # in approximate (FP8) score: the 4th / 5th partition, or the 200th /
+    # 201st candidate of the probed union (the GPU sums the FP8 products in
+    # fp32, the oracle in fp64)
+    top_c, sc_c = oracle.select_partitions_fp8(Qb, C, 5)
+    q8, qs = oracle.quantize_rows_fp8(Qb)
+    for q in bad:
+        near = abs(sc_c[q, 3] - sc_c[q, 4]) <= 1e-5 * abs(sc_c[q, 3])
+        mem = np.unique(np.concatenate([ids[off[p]:off[p + 1]] for p in top_c[q, :4]]))
+        x8, xs = oracle.quantize_rows_fp8(Xb[mem])
+        approx = np.sort((x8.astype(np.float64) @ q8[q].astype(np.float64)) * xs * qs[q])[::-1]
+        if approx.size > 200:
+            near = near or (approx[199] - approx[200]) <= 1e-5 * abs(approx[199])
+        assert near, f"query {q} differs without a near-tie in the oracle's approximate scores"
     ix.close()
 
 
