@@ -401,13 +401,48 @@ __global__ void all_partitions(int32_t* __restrict__ top, int64_t nq, int c) {
 // then a scatter that also records each pair's position (the inverse map).
 // The order of the pairs inside a partition is immaterial to the search.
 __global__ void pair_counts(const int32_t* __restrict__ top, int64_t nq, int tmax, const int32_t* __restrict__ tpq,
-                            int c, unsigned long long* __restrict__ cnt) {
+                            int c, unsigned long long* __restrict__ cnt, unsigned* __restrict__ first) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nq * tmax) return;
   const int64_t q = e / tmax;
   const int j = (int)(e - q * tmax);
   const int tq = tpq ? min(max(tpq[q], 1), tmax) : tmax;
   atomicAdd(&cnt[j < tq ? top[e] : c], 1ull);
+  if (first && j == 0) atomicAdd(&first[top[e]], 1u);
+}
+
+// The scan's partition order: the partitions that are the first probe of the
+// most queries come first (their finished items publish those queries' bounds
+// early), ties in the index's size order.  A counting rank in one launch: lane
+// l of block b ranks partition size_order[32 b + l] against every other, the
+// block's 8 warps splitting the comparisons; it costs less than a multi-pass
+// radix sort's launches while c is small (c <= kRankMaxC).
+constexpr int kRankTile = 4096;
+constexpr int kRankMaxC = 16384;
+
+__global__ void __launch_bounds__(256) first_probe_order(const int32_t* __restrict__ size_order,
+                                                         const unsigned* __restrict__ first, int c,
+                                                         int32_t* __restrict__ order) {
+  __shared__ unsigned sk[kRankTile];
+  __shared__ int rank_s[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + lane;
+  if (threadIdx.x < 32) rank_s[threadIdx.x] = 0;
+  const unsigned ki = i < c ? first[size_order[i]] : 0u;
+  int rank = 0;
+  for (int j0 = 0; j0 < c; j0 += kRankTile) {
+    const int m = min(kRankTile, c - j0);
+    __syncthreads();
+    for (int j = threadIdx.x; j < m; j += blockDim.x) sk[j] = first[size_order[j0 + j]];
+    __syncthreads();
+    for (int j = warp; j < m; j += 8) {
+      const unsigned kj = sk[j];
+      rank += (kj > ki) || (kj == ki && j0 + j < i);
+    }
+  }
+  atomicAdd(&rank_s[lane], rank);
+  __syncthreads();
+  if (warp == 0 && i < c) order[rank_s[lane]] = size_order[i];
 }
 
 __global__ void pair_scatter(const int32_t* __restrict__ top, int64_t nq, int tmax, const int32_t* __restrict__ tpq,
@@ -862,6 +897,7 @@ void select_prepared(const IndexData& ix, const float* Qf, const float* qscale, 
 }
 
 struct Grouped {
+  const int32_t* order;    // [c] partitions in the order their items are handed out
   int64_t* pair_off;       // [c + 1]
   const int32_t* vals;     // pairs sorted by partition (value q * t + j)
   int32_t* item_base;      // [c + 1]
@@ -872,19 +908,31 @@ struct Grouped {
 // map inv[q * t + j] = grouped position, and the work items (partition,
 // <= qb pairs) counted over partitions in size order.
 Grouped group_pairs(const IndexData& ix, int64_t nq, int t, const int32_t* tpq, int qb, const int32_t* top,
-                    int32_t* inv, cudaStream_t s, Scratch& scr) {
+                    int32_t* inv, cudaStream_t s, Scratch& scr, bool first_probes_first = false) {
   const int64_t P = nq * t;
   const int c = ix.c;
   stage_mark(s, "group", true);
-  unsigned long long* cnt = scr.get<unsigned long long>((size_t)c + 2);
+  // the pair counts [c + 2], then (first-probe order only) the first-probe
+  // counts [c] in the same allocation, cleared by one memset
+  const bool by_first = first_probes_first && c <= kRankMaxC;
+  const size_t words = (size_t)c + 2 + (by_first ? ((size_t)c + 1) / 2 : 0);
+  unsigned long long* cnt = scr.get<unsigned long long>(words);
   int32_t* cursor = scr.get<int32_t>((size_t)c + 1);
-  SOAR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * (c + 2), s));
-  pair_counts<<<ceil_div(P, 256), 256, 0, s>>>(top, nq, t, tpq, c, cnt);
+  SOAR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * words, s));
+  unsigned* first = by_first ? reinterpret_cast<unsigned*>(cnt + c + 2) : nullptr;
+  pair_counts<<<ceil_div(P, 256), 256, 0, s>>>(top, nq, t, tpq, c, cnt, first);
   SOAR_LAUNCHED();
   Grouped g;
+  g.order = ix.part_order;
+  if (first) {
+    int32_t* order = scr.get<int32_t>(c);
+    first_probe_order<<<ceil_div(c, 32), 256, 0, s>>>(ix.part_order, first, c, order);
+    SOAR_LAUNCHED();
+    g.order = order;
+  }
   g.pair_off = scr.get<int64_t>((size_t)c + 2);
   g.item_base = scr.get<int32_t>((size_t)c + 1);
-  group_offsets<<<1, kOffThreads, 0, s>>>(cnt, c, ix.part_order, qb, g.pair_off, g.item_base, cursor);
+  group_offsets<<<1, kOffThreads, 0, s>>>(cnt, c, g.order, qb, g.pair_off, g.item_base, cursor);
   SOAR_LAUNCHED();
   int32_t* vals = scr.get<int32_t>(P);
   pair_scatter<<<ceil_div(P, 256), 256, 0, s>>>(top, nq, t, tpq, c, g.pair_off, cursor, vals, inv);
@@ -901,7 +949,7 @@ void ivf_scan_typed(const IndexData& ix, const float* Qf, const float* qscale, i
                     cudaStream_t s, Scratch& scr) {
   const int qb = scan_qb(scan_xs<RowT>(ix.row_stride), len);
   Grouped g = group_pairs(ix, nq, t, tpq, qb, top, inv, s, scr);
-  IvfWork work{ix.offsets, g.pair_off, g.vals, ix.part_order, g.item_base, ix.c, t, qb};
+  IvfWork work{ix.offsets, g.pair_off, g.vals, g.order, g.item_base, ix.c, t, qb};
   launch_scan<RowT, IvfWork>(work, 1, g.max_items, static_cast<const RowT*>(ix.vectors), ix.row_stride, ix.ids,
                              ix.row_scales, Qf, qscale, len, qb, partials, s, scr);
 }
@@ -979,8 +1027,8 @@ void search(const IndexData& ix, const void* Q, soar_dtype dt, int64_t nq, int32
     int32_t* inv = scr.get<int32_t>(P);
     const int len = scan_tc_list_len(k);
     Cand* lists = scr.get<Cand>((size_t)P * len);
-    Grouped g = group_pairs(ix, nq, t, tpq, 128, top, inv, s, scr);
-    IvfWork work{ix.offsets, g.pair_off, g.vals, ix.part_order, g.item_base, ix.c, t, 128};
+    Grouped g = group_pairs(ix, nq, t, tpq, 128, top, inv, s, scr, true);
+    IvfWork work{ix.offsets, g.pair_off, g.vals, g.order, g.item_base, ix.c, t, 128};
     if (scan_tc_search(ix, work, g.max_items, Qf, qn, top, inv, tpq, nq, t, k, lists, device_error_word(), ids_out,
                        scores_out, s, scr))
       return;                                   // rescored and merged by the scan's finishing kernel
@@ -1128,7 +1176,7 @@ void exact_mips(const void* X, soar_dtype xdt, int64_t n, int32_t d, const void*
         int32_t* inv = bs.get<int32_t>((size_t)m * c);
         Cand* lists = bs.get<Cand>((size_t)m * c * len);
         Grouped g = group_pairs(fx, m, c, nullptr, 128, top, inv, s, bs);
-        IvfWork work{fx.offsets, g.pair_off, g.vals, fx.part_order, g.item_base, c, c, 128};
+        IvfWork work{fx.offsets, g.pair_off, g.vals, g.order, g.item_base, c, c, 128};
         if (!scan_tc_search(fx, work, g.max_items, Qf, qn, top, inv, nullptr, m, c, k, lists, device_error_word(),
                             ids_out + q0 * k, scores_out + q0 * k, s, bs)) {
           const int smem = 4 * c * (int)sizeof(uint16_t);
