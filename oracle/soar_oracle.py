@@ -35,6 +35,7 @@ __all__ = [
     "build_ivf", "select_partitions", "ivf_search", "partition_positions",
     "kmr_curve", "datapoints_searched", "probe_labels", "fp8_e4m3_round",
     "quantize_rows_fp8", "select_partitions_fp8", "precision_search", "bf16_round",
+    "multilevel_select", "multilevel_search",
 ]
 
 
@@ -326,6 +327,54 @@ def ivf_search(Q, X, C, offsets, ids, k: int, t: int, t_per_query=None):
         tq = t if t_per_query is None else int(t_per_query[i])
         parts = top[i, :tq]
         mem = np.concatenate([ids[offsets[p]:offsets[p + 1]] for p in parts]) if tq else np.empty(0, np.int32)
+        mem = np.unique(mem).astype(np.int64)
+        s = np.asarray(X[mem], dtype=F64) @ Q[i]
+        out_i[i], out_s[i] = topk_desc(s, k, mem)
+    return out_i, out_s
+
+
+# --------------------------------------------------------------------------
+# Multi-level VQ (App. A.4, general index setup; Section 4)
+# --------------------------------------------------------------------------
+
+def multilevel_select(Q, C, C2, offsets2, ids2, t: int, t1: int):
+    """Partition selection through a second VQ level.
+
+    The fine centroids C (c x d) are themselves vector-quantized by a coarse
+    codebook C2 into an IVF index over the rows of C (``offsets2``, ``ids2``
+    from ``build_ivf``; a fine centroid may be spilled to several coarse
+    partitions, since SOAR assigns at each level of the tree, Section 4).  A
+    query ranks the coarse partitions by <q, C2_j>, probes the top t1, takes
+    the union of their fine centroids (a spilled one counts once) and keeps
+    the t with the largest <q, C_i>, higher score first, lower id on ties.
+    That is an IVF search over the centroids (``ivf_search`` with C as the
+    datapoints and k = t).  When the probed coarse partitions hold fewer than
+    t fine centroids the rest of the row is padding (id -1, score -inf).
+    Returns ids int64 [nq, t] and scores f64 [nq, t].
+    """
+    return ivf_search(Q, C, C2, offsets2, ids2, t, t1)
+
+
+def multilevel_search(Q, X, C, offsets, ids, C2, offsets2, ids2, k: int, t: int, t1: int):
+    """IVF search whose probed partitions come from ``multilevel_select``.
+
+    Per query: the fine partitions it returns (padding dropped), the union of
+    their members with spilled copies removed, and the exact top-k by
+    <q, x> (fp64).  A query whose coarse probes hold no fine centroid probes
+    nothing and gets only padding.  Returns ids int64 [nq, k] (-1 padded) and
+    scores f64 [nq, k] (-inf padded).
+    """
+    Q = np.asarray(Q, dtype=F64)
+    top, _ = multilevel_select(Q, C, C2, offsets2, ids2, t, t1)
+    nq = Q.shape[0]
+    out_i = np.empty((nq, k), dtype=np.int64)
+    out_s = np.empty((nq, k), dtype=F64)
+    for i in range(nq):
+        parts = top[i][top[i] >= 0]
+        if parts.size:
+            mem = np.concatenate([ids[offsets[p]:offsets[p + 1]] for p in parts])
+        else:
+            mem = np.empty(0, np.int32)
         mem = np.unique(mem).astype(np.int64)
         s = np.asarray(X[mem], dtype=F64) @ Q[i]
         out_i[i], out_s[i] = topk_desc(s, k, mem)

@@ -552,3 +552,90 @@ def test_mlp_adam_three_steps_by_hand():
         assert p["b1"][0] == pytest.approx(w - 1.0, rel=1e-12)
     assert m["W2"][0, 0] == pytest.approx(0.091, rel=1e-12)
     assert v["W2"][0, 0] == pytest.approx(0.002997001, rel=1e-12)
+
+
+# ---------------------------------------------------------------- multi-level VQ
+
+def _two_level(seed=31, c=40, c2=5, s2=1):
+    """The small index above with c = 40 fine partitions whose centroids are
+    quantized again into c2 coarse partitions (SOAR, lambda = 1, s2 spills)."""
+    X, Q, C, A, off, ids = _small_index(seed=seed, c=c)
+    rng = np.random.default_rng(seed + 1)
+    C2 = oracle.kmeans(C, rng.choice(c, c2, replace=False), 4)
+    A2 = oracle.soar_assign(C, C2, 1.0, s2)
+    off2, ids2 = oracle.build_ivf(A2, c2)
+    return X, Q, C, A, off, ids, C2, A2, off2, ids2
+
+
+@pytest.mark.parametrize("t", [1, 7, 40])
+def test_multilevel_with_every_coarse_partition_is_flat(t):
+    # every fine centroid sits in at least one coarse partition, so probing
+    # all of them ranks all of C: the flat top-t selection and flat search
+    X, Q, C, A, off, ids, C2, A2, off2, ids2 = _two_level()
+    top, sc = oracle.multilevel_select(Q, C, C2, off2, ids2, t, C2.shape[0])
+    want, wsc = oracle.select_partitions(Q, C, t)
+    np.testing.assert_array_equal(top, want)
+    np.testing.assert_allclose(sc, wsc, rtol=1e-12)
+    gi, gs = oracle.multilevel_search(Q, X, C, off, ids, C2, off2, ids2, 10, t, C2.shape[0])
+    wi, ws = oracle.ivf_search(Q, X, C, off, ids, 10, t)
+    np.testing.assert_array_equal(gi, wi)
+    np.testing.assert_allclose(gs, ws, rtol=1e-12)
+
+
+def _select_by_loops(q, C, C2, A2, t, t1):
+    """Pure-Python two-level selection: coarse dot products by loops, the top
+    t1 coarse partitions, the fine centroids assigned to any of them, their
+    dot products by loops, the top t (score desc, lower id first), padded."""
+    dot = lambda u, v: sum(float(a) * float(b) for a, b in zip(u, v))
+    cs = [dot(q, C2[j]) for j in range(len(C2))]
+    probed = set(sorted(range(len(C2)), key=lambda j: (-cs[j], j))[:t1])
+    fine = [i for i in range(len(C)) if probed & set(int(a) for a in A2[i])]
+    fs = {i: dot(q, C[i]) for i in fine}
+    best = sorted(fine, key=lambda i: (-fs[i], i))[:t]
+    return best + [-1] * (t - len(best)), [fs[i] for i in best] + [-math.inf] * (t - len(best))
+
+
+@pytest.mark.parametrize("t,t1", [(1, 1), (4, 1), (30, 1), (6, 2), (12, 3)])
+def test_multilevel_select_by_loops(t, t1):
+    X, Q, C, A, off, ids, C2, A2, off2, ids2 = _two_level()
+    top, sc = oracle.multilevel_select(Q[:8], C, C2, off2, ids2, t, t1)
+    for i in range(8):
+        want_i, want_s = _select_by_loops(Q[i], C, C2, A2, t, t1)
+        assert list(top[i]) == want_i
+        np.testing.assert_allclose(sc[i], want_s, rtol=1e-12)
+
+
+def test_multilevel_search_is_topk_of_selected_partitions():
+    X, Q, C, A, off, ids, C2, A2, off2, ids2 = _two_level()
+    t, t1 = 6, 2
+    got_i, _ = oracle.multilevel_search(Q[:6], X, C, off, ids, C2, off2, ids2, 10, t, t1)
+    for i in range(6):
+        parts, _ = _select_by_loops(Q[i], C, C2, A2, t, t1)
+        parts = set(p for p in parts if p >= 0)
+        allowed = [j for j in range(X.shape[0]) if set(int(a) for a in A[j]) & parts]
+        s = X[allowed].astype(float) @ Q[i].astype(float)
+        want = [allowed[j] for j in sorted(range(len(allowed)), key=lambda j: (-s[j], allowed[j]))[:10]]
+        assert list(got_i[i]) == want
+
+
+def test_multilevel_empty_coarse_partition_gives_padding():
+    # a coarse centroid far out along u holds no fine centroid (every fine
+    # centroid lies within the unit ball); the query u ranks it first, so
+    # with t1 = 1 it probes nothing and gets only padding
+    X, Q, C, A, off, ids, C2, A2, off2, ids2 = _two_level(s2=1)
+    u = np.zeros(C.shape[1])
+    u[0] = 1.0
+    C2e = np.vstack([C2, 100.0 * u])
+    A2e = oracle.soar_assign(C, C2e, 1.0, 1)
+    assert not np.any(A2e == C2e.shape[0] - 1)
+    off2e, ids2e = oracle.build_ivf(A2e, C2e.shape[0])
+    neg = Q[Q[:, 0] < -0.05][:3]                 # queries that rank the far centroid last
+    Qe = np.vstack([u, neg]).astype(np.float32)
+    top, sc = oracle.multilevel_select(Qe, C, C2e, off2e, ids2e, 5, 1)
+    assert np.all(top[0] == -1) and np.all(np.isneginf(sc[0]))
+    gi, gs = oracle.multilevel_search(Qe, X, C, off, ids, C2e, off2e, ids2e, 10, 5, 1)
+    assert np.all(gi[0] == -1) and np.all(np.isneginf(gs[0]))
+    assert np.all(gi[1:] >= 0)
+    # with two coarse probes the query reaches the next coarse partition
+    top2, _ = oracle.multilevel_select(Qe[:1], C, C2e, off2e, ids2e, 5, 2)
+    assert np.all(top2[0] >= 0)
