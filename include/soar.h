@@ -194,7 +194,8 @@ SOAR_API soar_status soar_select_partitions(const soar_index* index, const void*
  * IVF search with deduplication of spilled copies (Section 2.2, Section 3.5).
  *   Q           [nq][d] queries (dtype)
  *   t           partitions probed per query (1 <= t <= min(c, 8192))
- *   t_per_query [nq] int32 per-query probe counts in [1, t], or NULL for t everywhere
+ *   t_per_query [nq] int32 per-query probe counts in [0, t] (values outside are
+ *               clamped; 0 probes nothing and gives only padding), or NULL for t everywhere
  *   rescore     SOAR_SCORE_FP8 indices: candidates kept per query for exact fp32
  *               rescoring (k <= rescore <= 4096); ignored (pass 0) for SOAR_SCORE_F32
  *   ids_out     [nq][k] int64 point ids, scores_out [nq][k] fp32 <q, x>
@@ -203,6 +204,54 @@ SOAR_API soar_status soar_select_partitions(const soar_index* index, const void*
 SOAR_API soar_status soar_search(const soar_index* index, const void* Q, soar_dtype dtype, int64_t nq,
                         int32_t k, int32_t t, const int32_t* t_per_query, int32_t rescore,
                         int64_t* ids_out, float* scores_out, cudaStream_t stream);
+
+/* ------------------------------------------------------------------ *
+ * Multi-level VQ (App. A.4, general index setup; Section 4).  The fine
+ * centroids of an index (c of them, often millions) are vector-quantized
+ * again into c2 coarse partitions, with SOAR spilling at that level too
+ * (the multiple assignments happen at each level of the tree).  The coarse
+ * level is an ordinary soar_index whose n = c rows are the fine centroids
+ * (fp32, mode SOAR_SCORE_F32), so partition selection (S = Q C^T, top t,
+ * Section 2.2) becomes an IVF search over the centroids: probe the t1
+ * coarse partitions of largest <q, C2_j>, take the union of their fine
+ * centroids (a spilled one counts once) and keep the t of largest <q, C_i>
+ * (score descending, lower id first on ties).  When the probed coarse
+ * partitions hold fewer than t fine centroids the query probes only those.
+ * ------------------------------------------------------------------ */
+
+/* Builds the coarse index of `index`: k-means over its c fine centroids
+ * (c2 clusters, `iters` Lloyd steps from the rows init_idx [c2] (device
+ * int32, distinct, in [0, c)), fp64 update as soar_train_centroids), then
+ * the primary and `spills` SOAR assignments with weight `lambda` (as
+ * soar_assign), then soar_index_build over those rows.  The fine index is
+ * only read.  *out owns its own device memory (free with soar_index_free).
+ * Requires 1 + spills <= c2 <= c, 0 <= spills <= 4, lambda finite >= 0. */
+SOAR_API soar_status soar_index_build_coarse(const soar_index* index, int32_t c2, int32_t iters,
+                                             const int32_t* init_idx, float lambda, int32_t spills,
+                                             soar_index** out, cudaStream_t stream);
+
+/* The two-level selection alone.
+ *   coarse    a coarse index (rows = the fine centroids, fp32)
+ *   Q         [nq][d] queries (dtype), device
+ *   t, t1     fine partitions kept (1 <= t <= min(c, 1024)), coarse partitions
+ *             probed (1 <= t1 <= min(c2, 8192))
+ *   top_out   [nq][t] int32 fine partition ids, best first, -1 after the last found
+ *   score_out [nq][t] fp32 <q, C_i> (-inf on padding), or NULL
+ *   count_out [nq] int32 number of fine partitions found (0 when every probed
+ *             coarse partition is empty) */
+SOAR_API soar_status soar_select_partitions_multilevel(const soar_index* coarse, const void* Q, soar_dtype dtype,
+                                                       int64_t nq, int32_t t, int32_t t1, int32_t* top_out,
+                                                       float* score_out, int32_t* count_out, cudaStream_t stream);
+
+/* soar_search with the probed partitions chosen by the two-level selection:
+ * the query probes the fine partitions soar_select_partitions_multilevel
+ * returns (fewer than t when fewer were found; none gives only padding).
+ * `coarse` must be a coarse index of `index` (n == index's c, same d, fp32).
+ * Other arguments and results as soar_search (t <= min(c, 1024)). */
+SOAR_API soar_status soar_search_multilevel(const soar_index* index, const soar_index* coarse, const void* Q,
+                                            soar_dtype dtype, int64_t nq, int32_t k, int32_t t, int32_t t1,
+                                            int32_t rescore, int64_t* ids_out, float* scores_out,
+                                            cudaStream_t stream);
 
 /*
  * Merge of m result lists per query into one top k (the exchange step of a

@@ -68,6 +68,9 @@ _SIGS = {
     "soar_quantize_fp8": ([_P, _I32, _I64, _I32, _P, _I32, _P, _P], _I32),
     "soar_merge_topk": ([_P, _P, _I64, _I32, _I32, _P, _I32, _P, _P, _P], _I32),
     "soar_select_partitions_static": ([_P, _P, _I32, _I64, _I32, _P, _P, _P], _I32),
+    "soar_index_build_coarse": ([_P, _I32, _I32, _P, _F32, _I32, ct.POINTER(_P), _P], _I32),
+    "soar_select_partitions_multilevel": ([_P, _P, _I32, _I64, _I32, _I32, _P, _P, _P, _P], _I32),
+    "soar_search_multilevel": ([_P, _P, _P, _I32, _I64, _I32, _I32, _I32, _I32, _P, _P, _P], _I32),
     "soar_check_device": ([], _I32),
     "soar_server_create": ([_P, ct.POINTER(ServerConfig), ct.POINTER(_P)], _I32),
     "soar_server_submit": ([_P, _P, _I32, _I32, ct.POINTER(ct.c_uint64)], _I32),
@@ -211,6 +214,10 @@ class Index:
     def row_scales(self) -> torch.Tensor:
         return self._view(self.info.row_scales, self.info.rows, torch.float32).clone()
 
+    def centroids(self) -> torch.Tensor:
+        i = self.info
+        return self._view(i.centroids, i.c * i.d, torch.float32).clone().view(i.c, i.d)
+
 
 class _DeviceArray:
     """Minimal __cuda_array_interface__ provider for memory the library owns."""
@@ -291,6 +298,40 @@ def soar_search(index: Index, Q: torch.Tensor, k: int, t: int, t_per_query=None,
     _check(load().soar_search(index.handle, _dev(Q, "Q", ndim=2), _dtype(Q), nq, k, t, tpq, rescore,
                               _dev(ids_out, "ids_out", torch.int64, 2),
                               _dev(scores_out, "scores_out", torch.float32, 2), _stream(stream)))
+    return ids_out, scores_out
+
+
+def soar_index_build_coarse(index: Index, c2: int, iters: int, init_idx: torch.Tensor, lam: float = 1.0,
+                            spills: int = 1, stream=None) -> Index:
+    """The coarse index of `index`: its fine centroids quantized into c2 partitions."""
+    h = ct.c_void_p()
+    _check(load().soar_index_build_coarse(index.handle, c2, iters, _dev(init_idx, "init_idx", torch.int32, 1),
+                                          lam, spills, ct.byref(h), _stream(stream)))
+    return Index(h)
+
+
+def soar_select_partitions_multilevel(coarse: Index, Q: torch.Tensor, t: int, t1: int, stream=None):
+    """(top [nq, t] int32, scores [nq, t], count [nq] int32) of the two-level selection."""
+    nq = Q.shape[0]
+    top = torch.empty((nq, t), dtype=torch.int32, device=Q.device)
+    sc = torch.empty((nq, t), dtype=torch.float32, device=Q.device)
+    cnt = torch.empty((nq,), dtype=torch.int32, device=Q.device)
+    _check(load().soar_select_partitions_multilevel(coarse.handle, _dev(Q, "Q", ndim=2), _dtype(Q), nq, t, t1,
+                                                    _dev(top, "top"), _dev(sc, "scores"), _dev(cnt, "count"),
+                                                    _stream(stream)))
+    return top, sc, cnt
+
+
+def soar_search_multilevel(index: Index, coarse: Index, Q: torch.Tensor, k: int, t: int, t1: int,
+                           rescore: int = 0, ids_out=None, scores_out=None, stream=None):
+    nq = Q.shape[0]
+    if ids_out is None:
+        ids_out = torch.empty((nq, k), dtype=torch.int64, device=Q.device)
+    if scores_out is None:
+        scores_out = torch.empty((nq, k), dtype=torch.float32, device=Q.device)
+    _check(load().soar_search_multilevel(index.handle, coarse.handle, _dev(Q, "Q", ndim=2), _dtype(Q), nq, k, t,
+                                         t1, rescore, _dev(ids_out, "ids_out", torch.int64, 2),
+                                         _dev(scores_out, "scores_out", torch.float32, 2), _stream(stream)))
     return ids_out, scores_out
 
 

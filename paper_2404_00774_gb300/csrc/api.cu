@@ -132,6 +132,14 @@ void* static_scratch() {
   return g_static_ptr[dev];
 }
 
+// A coarse index usable over an index of c fine partitions in d dimensions:
+// its rows are that index's fine centroids.
+void require_coarse_of(const soar_index* coarse, int32_t c, int32_t d) {
+  const soar::IndexData& x = coarse->data;
+  SOAR_REQUIRE(x.n == c && x.d == d, "the coarse index's rows must be the c fine centroids (n == c, same d)");
+  SOAR_REQUIRE(x.mode == SOAR_SCORE_F32 && x.dtype == SOAR_F32, "the coarse index must hold fp32 rows");
+}
+
 }  // namespace
 
 extern "C" {
@@ -280,6 +288,77 @@ soar_status soar_search(const soar_index* index, const void* Q, soar_dtype dtype
       SOAR_REQUIRE(rescore >= k && rescore <= 4096, "rescore must be in [k, 4096] for an FP8 index");
     soar::Scratch scr(stream);
     soar::search(index->data, Q, dtype, nq, k, t, t_per_query, rescore, ids_out, scores_out, stream, scr);
+  });
+}
+
+soar_status soar_index_build_coarse(const soar_index* index, int32_t c2, int32_t iters, const int32_t* init_idx,
+                                   float lambda, int32_t spills, soar_index** out, cudaStream_t stream) {
+  return guarded([&] {
+    SOAR_REQUIRE(index && init_idx && out, "null pointer");
+    const soar::IndexData& fine = index->data;
+    SOAR_REQUIRE(c2 >= 1 + spills && c2 <= fine.c, "c2 must be in [1 + spills, c]");
+    SOAR_REQUIRE(iters >= 0, "iters must be >= 0");
+    SOAR_REQUIRE(std::isfinite(lambda) && lambda >= 0.f, "lambda must be finite and >= 0");
+    SOAR_REQUIRE(spills >= 0 && spills <= 4, "spills must be in [0, 4]");
+    soar::Scratch scr(stream);
+    float* C2 = scr.get<float>((size_t)c2 * fine.d);
+    int32_t* A2 = scr.get<int32_t>((size_t)fine.c * (1 + spills));
+    soar::kmeans_train(fine.centroids, SOAR_F32, fine.c, fine.d, c2, iters, init_idx, C2, stream, scr);
+    soar::assign_points(fine.centroids, SOAR_F32, fine.c, fine.d, C2, c2, lambda, spills, A2, stream, scr);
+    soar_index* ix = new soar_index;
+    ix->data.n = fine.c;
+    ix->data.d = fine.d;
+    ix->data.c = c2;
+    ix->data.spills = spills;
+    ix->data.mode = SOAR_SCORE_F32;
+    ix->data.dtype = SOAR_F32;
+    ix->data.rows = (int64_t)fine.c * (1 + spills);
+    try {
+      soar::build_index(ix->data, fine.centroids, SOAR_F32, C2, A2, stream);
+    } catch (...) {
+      cudaStreamSynchronize(stream);
+      soar::free_index(ix->data);
+      delete ix;
+      throw;
+    }
+    *out = ix;
+  });
+}
+
+soar_status soar_select_partitions_multilevel(const soar_index* coarse, const void* Q, soar_dtype dtype, int64_t nq,
+                                              int32_t t, int32_t t1, int32_t* top_out, float* score_out,
+                                              int32_t* count_out, cudaStream_t stream) {
+  return guarded([&] {
+    SOAR_REQUIRE(coarse && Q && top_out && count_out, "null pointer");
+    SOAR_REQUIRE(valid_dtype(dtype), "unknown dtype");
+    const soar::IndexData& x = coarse->data;
+    SOAR_REQUIRE(x.mode == SOAR_SCORE_F32 && x.dtype == SOAR_F32, "the coarse index must hold fp32 rows");
+    SOAR_REQUIRE(nq >= 1 && nq * (int64_t)t < (int64_t(1) << 31) && nq * (int64_t)t1 < (int64_t(1) << 31),
+                 "nq * t and nq * t1 must be < 2^31");
+    SOAR_REQUIRE(t >= 1 && t <= x.n && t <= 1024, "t must be in [1, min(c, 1024)]");
+    SOAR_REQUIRE(t1 >= 1 && t1 <= x.c && t1 <= 8192, "t1 must be in [1, min(c2, 8192)]");
+    soar::Scratch scr(stream);
+    soar::multilevel_select(x, Q, dtype, nq, t, t1, top_out, score_out, count_out, stream, scr);
+  });
+}
+
+soar_status soar_search_multilevel(const soar_index* index, const soar_index* coarse, const void* Q,
+                                   soar_dtype dtype, int64_t nq, int32_t k, int32_t t, int32_t t1, int32_t rescore,
+                                   int64_t* ids_out, float* scores_out, cudaStream_t stream) {
+  return guarded([&] {
+    SOAR_REQUIRE(index && coarse && Q && ids_out && scores_out, "null pointer");
+    SOAR_REQUIRE(valid_dtype(dtype), "unknown dtype");
+    require_coarse_of(coarse, index->data.c, index->data.d);
+    SOAR_REQUIRE(nq >= 1 && nq * (int64_t)t < (int64_t(1) << 31) && nq * (int64_t)t1 < (int64_t(1) << 31),
+                 "nq * t and nq * t1 must be < 2^31");
+    SOAR_REQUIRE(k >= 1 && k <= 1024, "k must be in [1, 1024]");
+    SOAR_REQUIRE(t >= 1 && t <= index->data.c && t <= 1024, "t must be in [1, min(c, 1024)]");
+    SOAR_REQUIRE(t1 >= 1 && t1 <= coarse->data.c && t1 <= 8192, "t1 must be in [1, min(c2, 8192)]");
+    if (index->data.mode == SOAR_SCORE_FP8)
+      SOAR_REQUIRE(rescore >= k && rescore <= 4096, "rescore must be in [k, 4096] for an FP8 index");
+    soar::Scratch scr(stream);
+    soar::search(index->data, Q, dtype, nq, k, t, nullptr, rescore, ids_out, scores_out, stream, scr, &coarse->data,
+                 t1);
   });
 }
 

@@ -23,7 +23,7 @@ __global__ void query_bounds(const int2* __restrict__ hdr, const int32_t* __rest
                              const int32_t* __restrict__ tpq, float* __restrict__ lstar) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= nq) return;
-  const int tq = tpq ? min(max(tpq[q], 1), t) : t;
+  const int tq = tpq ? min(max(tpq[q], 0), t) : t;
   float best = -INFINITY;
   for (int j = 0; j < tq; ++j) best = fmaxf(best, __int_as_float(hdr[inv[q * t + j]].x));
   lstar[q] = best;
@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(256) rescore_wide(Cand* __restrict__ cand, con
   if (e >= P) return;
   const int64_t q = pair_vals[e] / t;
   const int j = pair_vals[e] - (int)(q * t);
-  if (tpq && j >= min(max(tpq[q], 1), t)) return;
+  if (tpq && j >= min(max(tpq[q], 0), t)) return;
   const int2 h = hdr[e];
   const int cnt = min(h.y & 0x7fffffff, kc);
   const bool ovf = h.y < 0;
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(256) finish_queries(
   const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (q >= nq) return;
-  const int tq = tpq ? min(max(tpq[q], 1), t) : t;
+  const int tq = tpq ? min(max(tpq[q], 0), t) : t;
   float lstar = -INFINITY;
   for (int j = lane; j < tq; j += 32) lstar = fmaxf(lstar, __int_as_float(hdr[inv[q * t + j]].x));
 #pragma unroll

@@ -150,9 +150,18 @@ size_t select_scratch_bytes(const IndexData& ix, int64_t nq);
 void select_partitions_in(const IndexData& ix, const void* Q, soar_dtype dt, int64_t nq, int32_t t, int32_t* top,
                           float* top_scores, void* scratch, cudaStream_t s);
 
+// With `coarse` set, the probed partitions come from multilevel_select
+// (t1 coarse probes) instead of the flat top-t selection.
 void search(const IndexData& ix, const void* Q, soar_dtype dt, int64_t nq, int32_t k, int32_t t,
             const int32_t* t_per_query, int32_t rescore, int64_t* ids_out, float* scores_out,
-            cudaStream_t s, Scratch& scr);
+            cudaStream_t s, Scratch& scr, const IndexData* coarse = nullptr, int32_t t1 = 0);
+
+// Two-level partition selection: an IVF search over the fine centroids (the
+// rows of `coarse`) with t1 coarse probes and k = t.  top [nq][t] fine
+// partition ids, best first, -1 after the last one found; count [nq] the
+// number found; top_scores [nq][t] (nullable) their <q, C_i>.
+void multilevel_select(const IndexData& coarse, const void* Q, soar_dtype dt, int64_t nq, int32_t t, int32_t t1,
+                       int32_t* top, float* top_scores, int32_t* count, cudaStream_t s, Scratch& scr);
 
 void merge_topk(const int64_t* ids, const float* scores, int64_t nq, int m, int len, const int64_t* id_offsets,
                 int k, int64_t* ids_out, float* scores_out, cudaStream_t s, Scratch& scr);

@@ -406,9 +406,9 @@ __global__ void pair_counts(const int32_t* __restrict__ top, int64_t nq, int tma
   if (e >= nq * tmax) return;
   const int64_t q = e / tmax;
   const int j = (int)(e - q * tmax);
-  const int tq = tpq ? min(max(tpq[q], 1), tmax) : tmax;
+  const int tq = tpq ? min(max(tpq[q], 0), tmax) : tmax;
   atomicAdd(&cnt[j < tq ? top[e] : c], 1ull);
-  if (first && j == 0) atomicAdd(&first[top[e]], 1u);
+  if (first && j == 0 && tq > 0) atomicAdd(&first[top[e]], 1u);
 }
 
 // The scan's partition order: the partitions that are the first probe of the
@@ -452,7 +452,7 @@ __global__ void pair_scatter(const int32_t* __restrict__ top, int64_t nq, int tm
   if (e >= nq * tmax) return;
   const int64_t q = e / tmax;
   const int j = (int)(e - q * tmax);
-  const int tq = tpq ? min(max(tpq[q], 1), tmax) : tmax;
+  const int tq = tpq ? min(max(tpq[q], 0), tmax) : tmax;
   const int b = j < tq ? top[e] : c;
   const int64_t pos = pair_off[b] + atomicAdd(&cursor[b], 1);
   vals[pos] = (int32_t)e;
@@ -683,7 +683,7 @@ __global__ void __launch_bounds__(128) merge_kernel(const Cand* __restrict__ par
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t q = (int64_t)blockIdx.x * 4 + w;
   if (q >= nq) return;
-  const int nl = kIvf ? (tpq ? min(max(tpq[q], 1), tmax) : tmax) : nrc;
+  const int nl = kIvf ? (tpq ? min(max(tpq[q], 0), tmax) : tmax) : nrc;
   uint16_t* head = heads_all + w * (kIvf ? tmax : nrc);
   for (int j = lane; j < nl; j += 32) head[j] = 0;
   __syncwarp();
@@ -1009,9 +1009,34 @@ void select_partitions_in(const IndexData& ix, const void* Q, soar_dtype dt, int
   SOAR_LAUNCHED();
 }
 
+// Fine probes from an IVF search over the fine centroids: its ids (int64,
+// best first, -1 padding after the last one found) become int32 partition
+// ids, and the number found is the query's probe count.  Entry e = q * t + j
+// writes top[e]; the last entry found (or j = 0 when none is) writes the count.
+__global__ void fine_probes(const int64_t* __restrict__ ids, int64_t total, int t, int32_t* __restrict__ top,
+                            int32_t* __restrict__ count) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  const int64_t q = e / t;
+  const int j = (int)(e - q * t);
+  const int64_t v = ids[e];
+  top[e] = v >= 0 ? (int32_t)v : -1;
+  if (v >= 0 && (j == t - 1 || ids[e + 1] < 0)) count[q] = j + 1;
+  if (j == 0 && v < 0) count[q] = 0;
+}
+
+void multilevel_select(const IndexData& coarse, const void* Q, soar_dtype dt, int64_t nq, int32_t t, int32_t t1,
+                       int32_t* top, float* top_scores, int32_t* count, cudaStream_t s, Scratch& scr) {
+  int64_t* ids = scr.get<int64_t>((size_t)nq * t);
+  float* sc = top_scores ? top_scores : scr.get<float>((size_t)nq * t);
+  search(coarse, Q, dt, nq, t, t1, nullptr, 0, ids, sc, s, scr);
+  fine_probes<<<ceil_div(nq * t, 256), 256, 0, s>>>(ids, nq * t, t, top, count);
+  SOAR_LAUNCHED();
+}
+
 void search(const IndexData& ix, const void* Q, soar_dtype dt, int64_t nq, int32_t k, int32_t t,
             const int32_t* tpq, int32_t rescore, int64_t* ids_out, float* scores_out, cudaStream_t s,
-            Scratch& scr) {
+            Scratch& scr, const IndexData* coarse, int32_t t1) {
   const bool fp8 = ix.mode == SOAR_SCORE_FP8;
   if (!fp8 && ix.tc_rows && k <= scan_tc_max_k(ix)) {
     // fp32 index: tensor-core screening with exact fp32 rescoring
@@ -1021,7 +1046,13 @@ void search(const IndexData& ix, const void* Q, soar_dtype dt, int64_t nq, int32
     stage_mark(s, "select", true);
     prep_any(Q, dt, nq, ix.d, qstride, false, Qf, nullptr, s, qn);   // rows and their norms
     int32_t* top = scr.get<int32_t>((size_t)nq * t);
-    select_prepared(ix, Qf, nullptr, nq, qstride, t, top, nullptr, s, scr);
+    if (coarse) {
+      int32_t* found = scr.get<int32_t>(nq);
+      multilevel_select(*coarse, Q, dt, nq, t, t1, top, nullptr, found, s, scr);
+      tpq = found;
+    } else {
+      select_prepared(ix, Qf, nullptr, nq, qstride, t, top, nullptr, s, scr);
+    }
     stage_mark(s, "select", false);
     const int64_t P = nq * t;
     int32_t* inv = scr.get<int32_t>(P);
@@ -1051,7 +1082,13 @@ void search(const IndexData& ix, const void* Q, soar_dtype dt, int64_t nq, int32
   stage_mark(s, "select", true);
   prep_any(Q, dt, nq, ix.d, qstride, fp8, Qf, qscale, s);
   int32_t* top = scr.get<int32_t>((size_t)nq * t);
-  select_prepared(ix, Qf, qscale, nq, qstride, t, top, nullptr, s, scr);
+  if (coarse) {
+    int32_t* found = scr.get<int32_t>(nq);
+    multilevel_select(*coarse, Q, dt, nq, t, t1, top, nullptr, found, s, scr);
+    tpq = found;
+  } else {
+    select_prepared(ix, Qf, qscale, nq, qstride, t, top, nullptr, s, scr);
+  }
   stage_mark(s, "select", false);
   const int64_t P = nq * t;
   int32_t* inv = scr.get<int32_t>(P);
