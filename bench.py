@@ -66,7 +66,10 @@ def parse_args():
     p.add_argument("--cpu-sample", type=int, default=300, help="queries timed on the CPU oracle")
     p.add_argument("--no-extras", action="store_true", help="skip the learned-probe and serving measurements")
     p.add_argument("--no-at-size", action="store_true",
-                   help="skip the precision (10^7 points) and serving (10^8 points) workloads at full size")
+                   help="skip the precision (10^7 points), serving (10^8 points) and multi-level (10^5 "
+                        "partitions) workloads at full size")
+    p.add_argument("--leg", choices=["precision", "serving", "multilevel"], default=None,
+                   help="run one full-size workload alone and print its results")
     p.add_argument("--arms", choices=["all", "main"], default="all",
                    help="all: SOAR at lambda 0.5/1/2, spill without SOAR, no spill; main: the timed arm only")
     return p.parse_args()
@@ -151,13 +154,15 @@ def datapoints_searched(sb, index, Qd, t, offsets):
     return sizes[top].sum(dim=1), top
 
 
-def find_t(sb, index, Qd, truth, k, t_max, target=RECALL_TARGET, cache=None):
-    """Smallest t in [1, t_max] with mean recall@k >= target (recall is monotone in t)."""
+def find_t(sb, index, Qd, truth, k, t_max, target=RECALL_TARGET, cache=None, search=None):
+    """Smallest t in [1, t_max] with mean recall@k >= target (recall is monotone
+    in t); ``search(t) -> ids`` replaces the plain soar_search when given."""
     cache = {} if cache is None else cache
+    search = search or (lambda t: sb.soar_search(index, Qd, k, t)[0])
 
     def rec(t):
         if t not in cache:
-            ids, _ = sb.soar_search(index, Qd, k, t)
+            ids = search(t)
             cache[t] = float(recall_at_k(ids, truth).mean())
         return cache[t]
     lo, hi = 1, t_max
@@ -592,6 +597,9 @@ def precision_at_size(sb, dev, steps, warmup, n_train=1_000_000, n_test=10_000, 
     C, km_ms = ev_ms(lambda: sb.soar_train_centroids(X[:train_rows], w.c, w.kmeans_iters, init))
     A, asg_ms = ev_ms(lambda: sb.soar_assign(X, C, w.lam, w.spills))
     ix, build_ms = ev_ms(lambda: sb.soar_index_build(X, C, A))
+    # the same assignment in the FP8 form: FP8 codes with per-row scales for
+    # every copy, one bf16 copy of the rows for the exact rescoring
+    ix8, build8_ms = ev_ms(lambda: sb.soar_index_build(X, C, A, mode=sb.SOAR_SCORE_FP8))
     del A
     truth, gt_ms = ev_ms(lambda: sb.soar_exact_mips(X, Q, w.k)[0])
     t_fix, rec_fix = find_t(sb, ix, Q, truth, w.k, 512)
@@ -623,6 +631,28 @@ def precision_at_size(sb, dev, steps, warmup, n_train=1_000_000, n_test=10_000, 
                                "frac": alg / (scan_ms / 1e3) / 1e9 / hbm, "peak_source": f"{src} hbm_gbs",
                                "rule": "distinct probed partitions x rows x (2d + 4) + queries + results"}}
     log(f"[bench] precision fixed t: {fixed}")
+    # ---- FP8 scoring of the probed union, the best `rescore` approximate
+    # scores rescored exactly from the bf16 copy
+    rescore = 1000
+    fp8_search = lambda t: sb.soar_search(ix8, Q, w.k, t, rescore=rescore)[0]
+    t8, rec8 = find_t(sb, ix8, Q, truth, w.k, 64, search=fp8_search)
+    if t8 is not None:
+        for _ in range(warmup):
+            fp8_search(t8)
+        ts8 = []
+        for i in range(steps):
+            flush.fill_(float(i))
+            ts8.append(ev_ms(lambda: fp8_search(t8))[1])
+        ms8 = statistics.mean(ts8)
+        fixed["fp8_rescore"] = {"t": t8, "recall": rec8, "rescore": rescore, "ms_per_step": ms8,
+                                "qps": n_test / (ms8 / 1e3), "build_ms": build8_ms,
+                                "index_bytes": int(ix8.info.device_bytes),
+                                "bf16_index_bytes": int(ix.info.device_bytes),
+                                "path": "SIMT FP8 scan, per-partition top-rescore lists, exact fp32 rescoring"}
+    else:
+        fixed["fp8_rescore"] = {"t": None, "recall_at_64": rec8, "rescore": rescore}
+    ix8.close()
+    log(f"[bench] precision FP8 + rescore: {fixed['fp8_rescore']}")
     # ---- learned probe count on this index
     t1 = time.perf_counter()
     Qtr = synth.sample_on_device(mix, n_train, 304, dev, torch.float32)
@@ -671,6 +701,82 @@ def precision_at_size(sb, dev, steps, warmup, n_train=1_000_000, n_test=10_000, 
 
 
 # ------------------------------------------------------------------ GPU arm
+
+def multilevel_at_size(sb, dev, steps, warmup, c2=1000, train_rows=1_000_000, coarse_iters=10,
+                       t1s=(4, 8, 16, 32, 64, 128)):
+    """Two-level partition selection (App. A.4, general index setup; Section
+    4) where flat selection costs: 10^7 unit vectors (d = 96, bf16, a
+    10 000-component isotropic mixture drawn on the device) in c = 10^5
+    partitions of ~100 rows (4 Lloyd iterations on the first 10^6 draws, SOAR
+    lambda = 1, one spill), the 10^5 centroids quantized again into c2 = 1 000
+    coarse partitions (10 Lloyd iterations, SOAR lambda = 1, one spill).
+    Flat selection (S = Q C^T over all 10^5 centroids, top t) is run at the
+    smallest t reaching recall@10 >= 0.9; the two-level selection probes t1
+    coarse partitions and keeps the same t.  Per t1: recall, selection ms
+    (the selection call alone), whole-search ms and QPS."""
+    import torch
+    w = synth.WORKLOADS["multilevel"]
+    mix = synth.mixture_for(w)
+    X = synth.sample_on_device(mix, w.n, w.data_seed, dev, torch.bfloat16)
+    Q = synth.sample_on_device(mix, w.nq, w.query_seed, dev, torch.float32)
+    stream = torch.cuda.current_stream()
+
+    def ev_ms(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        out = fn()
+        b.record(stream)
+        b.synchronize()
+        return out, a.elapsed_time(b)
+
+    init = torch.from_numpy(synth.init_indices(train_rows, w.c, w.init_seed)).to(dev)
+    C, km_ms = ev_ms(lambda: sb.soar_train_centroids(X[:train_rows], w.c, w.kmeans_iters, init))
+    A, asg_ms = ev_ms(lambda: sb.soar_assign(X, C, w.lam, w.spills))
+    ix, build_ms = ev_ms(lambda: sb.soar_index_build(X, C, A))
+    del A
+    init2 = torch.from_numpy(synth.init_indices(w.c, c2, w.init_seed + 1)).to(dev)
+    coarse, coarse_ms = ev_ms(lambda: sb.soar_index_build_coarse(ix, c2, coarse_iters, init2, 1.0, 1))
+    truth, gt_ms = ev_ms(lambda: sb.soar_exact_mips(X, Q, w.k)[0])
+    del X
+    t_flat, rec_flat = find_t(sb, ix, Q, truth, w.k, 1024)
+    if t_flat is None:               # the target is out of reach below t = 1024: report at 1024
+        t_flat = 1024
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        ts = []
+        for i in range(steps):
+            flush.fill_(float(i))
+            ts.append(ev_ms(fn)[1])
+        return statistics.mean(ts)
+
+    flat_search = timed(lambda: sb.soar_search(ix, Q, w.k, t_flat))
+    flat_select = timed(lambda: sb.soar_select_partitions(ix, Q, t_flat))
+    out = {"workload": f"multilevel: n={w.n} d={w.d} bf16 c={w.c} c2={c2} lambda={w.lam} spills={w.spills} "
+                       f"nq={w.nq} k={w.k}",
+           "build_ms": {"kmeans": km_ms, "assign": asg_ms, "index": build_ms, "coarse": coarse_ms,
+                        "ground_truth": gt_ms},
+           "flat": {"t": t_flat, "recall": rec_flat, "select_ms": flat_select, "search_ms": flat_search,
+                    "qps": w.nq / (flat_search / 1e3)},
+           "two_level": []}
+    for t1 in t1s:
+        if t1 > c2:
+            break
+        ids, _ = sb.soar_search_multilevel(ix, coarse, Q, w.k, t_flat, t1)
+        rec = float(recall_at_k(ids, truth).mean())
+        sel = timed(lambda: sb.soar_select_partitions_multilevel(coarse, Q, t_flat, t1))
+        srch = timed(lambda: sb.soar_search_multilevel(ix, coarse, Q, w.k, t_flat, t1))
+        out["two_level"].append({"t1": t1, "recall": rec, "select_ms": sel, "search_ms": srch,
+                                 "qps": w.nq / (srch / 1e3)})
+        log(f"[bench] two-level t1={t1}: recall {rec:.4f}, select {sel:.3f} ms, search {srch:.3f} ms")
+    best = [r for r in out["two_level"] if r["recall"] >= RECALL_TARGET]
+    out["two_level_at_target"] = max(best, key=lambda r: r["qps"]) if best else None
+    coarse.close()
+    ix.close()
+    return out
+
 
 def run_ours(args):
     import torch
@@ -915,6 +1021,11 @@ def run_ours(args):
             line["serving"] = serving_at_size(sb, dev)
         except Exception as e:   # reported, never fatal for the metric
             line["serving"] = {"error": str(e)[:300]}
+        torch.cuda.empty_cache()
+        try:
+            line["multilevel"] = multilevel_at_size(sb, dev, args.steps, args.warmup)
+        except Exception as e:   # reported, never fatal for the metric
+            line["multilevel"] = {"error": str(e)[:300]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -922,10 +1033,25 @@ def run_ours(args):
     return 0
 
 
+def run_leg(args):
+    """One full-size leg alone (its own index), printed as one JSON object."""
+    import torch
+    from paper_2404_00774_gb300 import binding as sb
+    sb.load()
+    dev = torch.device("cuda", 0)
+    legs = {"precision": lambda: precision_at_size(sb, dev, args.steps, args.warmup),
+            "serving": lambda: serving_at_size(sb, dev),
+            "multilevel": lambda: multilevel_at_size(sb, dev, args.steps, args.warmup)}
+    print(json.dumps({args.leg: legs[args.leg]()}), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.leg:
+        return run_leg(args)
     return run_ours(args)
 
 

@@ -60,6 +60,10 @@ WORKLOADS = {
                           10_000, 10_000, 10, 1.0, 1, 301, 302, 303, 300),
     "serving": Workload("serving", 100_000_000, 128, 4000, "isotropic", 0.3,
                         40_000, 10_000, 10, 1.0, 1, 501, 502, 503, 500),
+    # many partitions of ~100 rows, for the two-level (coarse over fine
+    # centroids) selection; 10 partitions per mixture component as above
+    "multilevel": Workload("multilevel", 10_000_000, 96, 10_000, "isotropic", 0.3,
+                           100_000, 10_000, 10, 1.0, 1, 601, 602, 603, 600, kmeans_iters=4),
 }
 
 
