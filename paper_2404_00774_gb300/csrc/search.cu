@@ -65,16 +65,6 @@ __device__ __forceinline__ float fp8_value(uint8_t b) {
   __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)b, __NV_E4M3);
   return __half2float(__half(h));
 }
-template <> struct Expand<uint8_t> {
-  static constexpr int kPer = 16;
-  __device__ static void to(uint4 v, float* dst) {
-    uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) dst[4 * i + b] = fp8_value((uint8_t)(w[i] >> (8 * b)));
-  }
-};
 
 // ------------------------------------------------------------ query prep
 
@@ -1054,6 +1044,12 @@ void search(const IndexData& ix, const void* Q, soar_dtype dt, int64_t nq, int32
       select_prepared(ix, Qf, nullptr, nq, qstride, t, top, nullptr, s, scr);
     }
     stage_mark(s, "select", false);
+    if (scan_by_query_usable(ix, nq, t, k)) {   // few queries per probed partition: query-major exact scan
+      stage_mark(s, "scan", true);
+      scan_by_query(ix, Qf, qstride, top, tpq, nq, t, k, ids_out, scores_out, s);
+      stage_mark(s, "scan", false);
+      return;
+    }
     const int64_t P = nq * t;
     int32_t* inv = scr.get<int32_t>(P);
     const int len = scan_tc_list_len(k);
@@ -1090,9 +1086,9 @@ void search(const IndexData& ix, const void* Q, soar_dtype dt, int64_t nq, int32
     select_prepared(ix, Qf, qscale, nq, qstride, t, top, nullptr, s, scr);
   }
   stage_mark(s, "select", false);
-  const int64_t P = nq * t;
-  int32_t* inv = scr.get<int32_t>(P);
   if (!fp8) {
+    const int64_t P = nq * t;
+    int32_t* inv = scr.get<int32_t>(P);
     Cand* partials = scr.get<Cand>((size_t)P * k);
     if (ix.dtype == SOAR_F32)
       ivf_scan_typed<float>(ix, Qf, qscale, nq, t, tpq, k, partials, inv, top, s, scr);
@@ -1107,17 +1103,12 @@ void search(const IndexData& ix, const void* Q, soar_dtype dt, int64_t nq, int32
     stage_mark(s, "merge", false);
     return;
   }
-  // FP8: per-partition lists of the best `len` approximate scores, merged to
-  // `rescore` distinct candidates per query, rescored exactly in fp32.
-  const int len = (int)std::min<int64_t>(rescore, std::max<int64_t>(ix.max_partition, 1));
-  Cand* partials = scr.get<Cand>((size_t)P * len);
-  ivf_scan_typed<uint8_t>(ix, Qf, qscale, nq, t, tpq, len, partials, inv, top, s, scr);
+  // FP8: the best `rescore` approximate scores of each query's probed union
+  // (each point once), rescored exactly in fp32 from the stored rows.
   int32_t* cand = scr.get<int32_t>((size_t)nq * rescore);
-  const int smem = 4 * t * (int)sizeof(uint16_t);
-  SOAR_CUDA(cudaFuncSetAttribute(merge_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  merge_kernel<true><<<ceil_div(nq, 4), 128, smem, s>>>(partials, len, nq, t, tpq, inv, 0, rescore, nullptr, cand,
-                                                        nullptr);
-  SOAR_LAUNCHED();
+  stage_mark(s, "scan", true);
+  fp8_shortlist(ix, Qf, qscale, top, tpq, nq, t, rescore, cand, s, scr);
+  stage_mark(s, "scan", false);
   float* work = scr.get<float>((size_t)nq * rescore);
   const int ostride = ix.dtype == SOAR_F32 ? (ix.d + 3) / 4 * 4 : (ix.d + 7) / 8 * 8;
   if (ix.dtype == SOAR_F32) {

@@ -1,0 +1,198 @@
+// Exact top-R shortlist of approximately scored candidates over each query's
+// probed union (Section 3.5: compressed representations are duplicated for
+// every assignment, the high-bitrate rows are stored once and rescore the
+// best candidates), for the FP8 layout: per-row scaled E4M3 codes of every
+// copy, approximate score s_q * s_x * sum q8 x8.
+//
+// Two kernels, a warp per query:
+//   approx_union  walks the query's probed partitions (lane = row, code rows
+//                 read coalesced), drops a copy when the point has another
+//                 copy in a partition the query probed earlier (from the
+//                 index's copy of the assignment: each point counts once),
+//                 and writes one 64-bit rank key per remaining point
+//                 (approximate score descending, then id ascending) into the
+//                 query's slice of a key buffer;
+//   select_top_r  finds the R smallest keys of the slice by an MSB-first
+//                 radix select over bytes (warp histograms in shared memory;
+//                 the keys are distinct, so the selected set is exact) and
+//                 writes their ids.
+// The caller rescores those ids exactly from the stored rows.
+#include "internal.cuh"
+#include "scan_common.cuh"
+
+namespace soar {
+
+namespace {
+
+constexpr int kSlWarps = 8;
+constexpr int kSlMaxProbesSmem = 256;   // probe lists held in shared memory up to this t
+
+__device__ __forceinline__ float fp8_code_value(uint32_t b) {
+  __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)b, __NV_E4M3);
+  return __half2float(__half(h));
+}
+
+__global__ void __launch_bounds__(32 * kSlWarps) approx_union_fp8(
+    const uint8_t* __restrict__ codes, int code_stride, const float* __restrict__ row_scales,
+    const int32_t* __restrict__ ids, const int64_t* __restrict__ off, const int32_t* __restrict__ assign, int a,
+    const float* __restrict__ Qf, const float* __restrict__ qscale, const int32_t* __restrict__ top,
+    const int32_t* __restrict__ tpq, int64_t q0, int64_t nq, int t, int64_t slice, uint64_t* __restrict__ keys,
+    int64_t* __restrict__ counts) {
+  constexpr unsigned kFull = 0xffffffffu;
+  extern __shared__ __align__(16) unsigned char sl_smem[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t ql = (int64_t)blockIdx.x * kSlWarps + w;   // query within this chunk
+  if (ql >= nq) return;                                   // uniform within the warp
+  const int64_t q = q0 + ql;
+  float* qs = reinterpret_cast<float*>(sl_smem) + w * code_stride;
+  int32_t* probes_s = reinterpret_cast<int32_t*>(reinterpret_cast<float*>(sl_smem) + kSlWarps * code_stride) +
+                      w * kSlMaxProbesSmem;
+  for (int i = lane; i < code_stride; i += 32) qs[i] = Qf[q * (int64_t)code_stride + i];
+  const int tq = tpq ? min(max(tpq[q], 0), t) : t;
+  const int32_t* probes = top + q * (int64_t)t;
+  if (t <= kSlMaxProbesSmem) {
+    for (int j = lane; j < tq; j += 32) probes_s[j] = probes[j];
+    probes = probes_s;
+  }
+  __syncwarp();
+  const float qsc = qscale[q];
+  uint64_t* out = keys + ql * slice;
+  int64_t n = 0;
+  for (int j = 0; j < tq; ++j) {
+    const int p = probes[j];
+    const int64_t r0 = off[p], r1 = off[p + 1];
+    for (int64_t rb = r0; rb < r1; rb += 32) {
+      const int64_t r = rb + lane;
+      bool keep = false;
+      uint64_t key = 0;
+      if (r < r1) {
+        const int32_t id = ids[r];
+        keep = true;
+        // the point's copy in an earlier-probed partition is the one that counts
+        for (int i = 0; i < a && keep; ++i) {
+          const int other = assign[(int64_t)id * a + i];
+          if (other == p) continue;
+          for (int jj = 0; jj < j; ++jj)
+            if (probes[jj] == other) { keep = false; break; }
+        }
+        if (keep) {
+          const uint4* x = reinterpret_cast<const uint4*>(codes + r * (int64_t)code_stride);
+          float acc = 0.f;
+          for (int c = 0; c < code_stride / 16; ++c) {
+            const uint4 v = __ldg(x + c);
+            const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+              for (int b = 0; b < 4; ++b) acc = fmaf(qs[16 * c + 4 * i + b], fp8_code_value((wv[i] >> (8 * b)) & 0xffu), acc);
+          }
+          key = rank_key(acc * qsc * row_scales[r], (uint32_t)id);
+        }
+      }
+      const unsigned bal = __ballot_sync(kFull, keep);
+      if (keep) out[n + __popc(bal & ((1u << lane) - 1u))] = key;
+      n += __popc(bal);
+    }
+  }
+  if (lane == 0) counts[ql] = n;
+}
+
+// The R smallest keys of each query's slice -> their ids (cand [nq][R],
+// padded with -1 when the slice holds fewer than R keys).
+__global__ void __launch_bounds__(32 * kSlWarps) select_top_r(const uint64_t* __restrict__ keys,
+                                                              const int64_t* __restrict__ counts, int64_t nq,
+                                                              int64_t slice, int R, int32_t* __restrict__ cand) {
+  constexpr unsigned kFull = 0xffffffffu;
+  __shared__ int hist_all[kSlWarps][256];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t ql = (int64_t)blockIdx.x * kSlWarps + w;
+  if (ql >= nq) return;
+  const uint64_t* K = keys + ql * slice;
+  const int64_t n = counts[ql];
+  int32_t* out = cand + ql * (int64_t)R;
+  int* hist = hist_all[w];
+  uint64_t limit = ~0ull;                 // keys <= limit are selected
+  if (n > R) {
+    uint64_t prefix = 0, mask = 0;
+    int64_t need = R;
+    for (int shift = 56; shift >= 0; shift -= 8) {
+      for (int b = lane; b < 256; b += 32) hist[b] = 0;
+      __syncwarp();
+      for (int64_t i = lane; i < n; i += 32) {
+        const uint64_t kk = K[i];
+        if ((kk & mask) == prefix) atomicAdd(&hist[(kk >> shift) & 0xff], 1);
+      }
+      __syncwarp();
+      // lane l owns bins 8l .. 8l+7; a warp scan of their sums finds the
+      // first bin whose inclusive count reaches `need`
+      int v[8], s = 0;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) { v[i] = hist[8 * lane + i]; s += v[i]; }
+      int incl = s;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const int excl = incl - s;
+      const unsigned hit = __ballot_sync(kFull, incl >= need);
+      const int owner = __ffs(hit) - 1;           // need <= total, so some lane hits
+      int bin = 0, before = 0, in_bin = 0;
+      if (lane == owner) {
+        int c = excl;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          if (c + v[i] >= need) { bin = 8 * lane + i; before = c; in_bin = v[i]; break; }
+          c += v[i];
+        }
+      }
+      bin = __shfl_sync(kFull, bin, owner);
+      before = __shfl_sync(kFull, before, owner);
+      in_bin = __shfl_sync(kFull, in_bin, owner);
+      prefix |= (uint64_t)bin << shift;
+      mask |= (uint64_t)0xff << shift;
+      if (before + in_bin == need || shift == 0) {   // the whole bin fits: done
+        limit = prefix | (shift ? (((uint64_t)1 << shift) - 1) : 0);
+        break;
+      }
+      need -= before;
+      __syncwarp();
+    }
+  }
+  int64_t m = 0;
+  for (int64_t i0 = 0; i0 < n; i0 += 32) {
+    const int64_t i = i0 + lane;
+    const bool take = i < n && K[i] <= limit;
+    const unsigned bal = __ballot_sync(kFull, take);
+    const int64_t pos = m + __popc(bal & ((1u << lane) - 1u));
+    if (take && pos < R) out[pos] = (int32_t)(K[i] & 0xffffffffu);
+    m += __popc(bal);
+  }
+  for (int64_t i = min(m, (int64_t)R) + lane; i < R; i += 32) out[i] = -1;
+}
+
+}  // namespace
+
+void fp8_shortlist(const IndexData& ix, const float* Qf, const float* qscale, const int32_t* top,
+                   const int32_t* tpq, int64_t nq, int t, int R, int32_t* cand, cudaStream_t s, Scratch& scr) {
+  const int64_t slice = std::max<int64_t>(1, std::min<int64_t>((int64_t)t * ix.max_partition, ix.rows));
+  // queries per pass so that the key buffer stays within 2 GB
+  const int64_t chunk = std::max<int64_t>(kSlWarps, std::min<int64_t>(nq, ((int64_t)1 << 28) / slice));
+  const int64_t cq = std::min(chunk, nq);
+  uint64_t* keys = scr.get<uint64_t>((size_t)cq * slice);
+  int64_t* counts = scr.get<int64_t>(cq);
+  const size_t smem = (size_t)kSlWarps * ix.code_stride * sizeof(float) + (size_t)kSlWarps * kSlMaxProbesSmem * 4;
+  SOAR_CUDA(cudaFuncSetAttribute(approx_union_fp8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int a = 1 + ix.spills;
+  for (int64_t q0 = 0; q0 < nq; q0 += cq) {
+    const int64_t m = std::min(cq, nq - q0);
+    approx_union_fp8<<<ceil_div(m, kSlWarps), 32 * kSlWarps, smem, s>>>(
+        static_cast<const uint8_t*>(ix.vectors), ix.code_stride, ix.row_scales, ix.ids, ix.offsets, ix.assign, a,
+        Qf, qscale, top, tpq, q0, m, t, slice, keys, counts);
+    SOAR_LAUNCHED();
+    select_top_r<<<ceil_div(m, kSlWarps), 32 * kSlWarps, 0, s>>>(keys, counts, m, slice, R, cand + q0 * R);
+    SOAR_LAUNCHED();
+  }
+}
+
+}  // namespace soar
