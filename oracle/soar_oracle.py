@@ -35,7 +35,8 @@ __all__ = [
     "build_ivf", "select_partitions", "ivf_search", "partition_positions",
     "kmr_curve", "datapoints_searched", "probe_labels", "fp8_e4m3_round",
     "quantize_rows_fp8", "select_partitions_fp8", "precision_search", "bf16_round",
-    "multilevel_select", "multilevel_search",
+    "multilevel_select", "multilevel_search", "pq_residuals", "pq_train", "pq_encode",
+    "pq_index_codes", "pq_search",
 ]
 
 
@@ -330,6 +331,85 @@ def ivf_search(Q, X, C, offsets, ids, k: int, t: int, t_per_query=None):
         mem = np.unique(mem).astype(np.int64)
         s = np.asarray(X[mem], dtype=F64) @ Q[i]
         out_i[i], out_s[i] = topk_desc(s, k, mem)
+    return out_i, out_s
+
+
+# --------------------------------------------------------------------------
+# Product quantization of the partitioning residuals (Section 3.5, App. A.3)
+# --------------------------------------------------------------------------
+
+PQ_DIMS = 2        # dimensions per subspace
+PQ_CENTRES = 16    # centres per subspace: 4-bit codes
+
+
+def pq_residuals(X, C, part):
+    """r = x - C[part] for every row, formed in fp32 (the stored precision of x and C)."""
+    return (np.asarray(X, dtype=np.float32) - np.asarray(C, dtype=np.float32)[np.asarray(part)]).astype(np.float32)
+
+
+def pq_train(R, iters: int, init_idx):
+    """PQ codebooks of residuals R [n, d] (d even): for each subspace s (dims
+    2s, 2s+1), Lloyd's k-means (``kmeans``) with 16 centres started from the
+    rows ``init_idx`` (16 distinct rows, the same for every subspace).
+    Returns B float32 [d/2, 16, 2]."""
+    R = np.asarray(R, dtype=np.float32)
+    n, d = R.shape
+    assert d % PQ_DIMS == 0 and len(init_idx) == PQ_CENTRES
+    return np.stack([kmeans(np.ascontiguousarray(R[:, PQ_DIMS * s:PQ_DIMS * (s + 1)]), init_idx, iters)
+                     for s in range(d // PQ_DIMS)])
+
+
+def pq_encode(R, B):
+    """code[i, s] = argmin_j ||R[i, 2s:2s+2] - B[s, j]||^2, lower j on ties
+    (``primary_assign`` per subspace).  Returns uint8 [n, d/2] (values < 16)."""
+    R = np.asarray(R, dtype=np.float32)
+    return np.stack([primary_assign(np.ascontiguousarray(R[:, PQ_DIMS * s:PQ_DIMS * (s + 1)]), B[s])[0]
+                     for s in range(B.shape[0])], axis=1).astype(np.uint8)
+
+
+def pq_index_codes(X, C, offsets, ids, B):
+    """The PQ code of every index row: row r is the copy of point ids[r] in
+    its partition p (offsets[p] <= r < offsets[p+1]), encoded from the
+    residual x - C_p, so a spilled point has one code per copy (Section 3.5:
+    the compressed form is duplicated, the full-precision row is not)."""
+    part = np.repeat(np.arange(len(offsets) - 1), np.diff(offsets))
+    return pq_encode(pq_residuals(np.asarray(X)[ids], C, part), B)
+
+
+def pq_search(Q, X, C, offsets, ids, B, codes, k: int, t: int, rescore: int, t_per_query=None):
+    """IVF search scoring the probed copies by their PQ codes, then exact rescoring.
+
+    approx(q, copy in p) = <q, C_p> + sum_s <q_s, B[s, code_s]> (fp64).
+    The top t partitions by <q, C> are probed in that order; a point met in
+    several of them is scored by its copy in the first (earliest-probed)
+    one.  The best ``rescore`` points by approximate score (higher first,
+    lower id on ties) are rescored exactly as <q, x> (fp64) and the top k of
+    those returned.  Returns (ids int64 [nq,k], exact scores f64 [nq,k]).
+    """
+    Q = np.asarray(Q, dtype=F64)
+    nq = Q.shape[0]
+    tmax = t if t_per_query is None else int(np.max(t_per_query))
+    top, _ = select_partitions(Q, C, tmax)
+    Cd, Bd = np.asarray(C, dtype=F64), np.asarray(B, dtype=F64)
+    out_i = np.empty((nq, k), dtype=np.int64)
+    out_s = np.empty((nq, k), dtype=F64)
+    m = Bd.shape[0]
+    for i in range(nq):
+        tq = t if t_per_query is None else int(t_per_query[i])
+        lut = np.einsum("sjd,sd->sj", Bd, Q[i].reshape(m, PQ_DIMS))       # <q_s, B[s, j]>
+        seen = {}
+        for p in top[i, :tq]:
+            base = float(Cd[p] @ Q[i])
+            for r in range(offsets[p], offsets[p + 1]):
+                pid = int(ids[r])
+                if pid not in seen:
+                    seen[pid] = base + float(lut[np.arange(m), codes[r]].sum())
+        mem = np.fromiter(seen.keys(), dtype=np.int64, count=len(seen))
+        approx = np.fromiter(seen.values(), dtype=F64, count=len(seen))
+        cand, _ = topk_desc(approx, rescore, mem)
+        cand = cand[cand >= 0]
+        exact = np.asarray(X[cand], dtype=F64) @ Q[i]
+        out_i[i], out_s[i] = topk_desc(exact, k, cand)
     return out_i, out_s
 
 

@@ -639,3 +639,118 @@ def test_multilevel_empty_coarse_partition_gives_padding():
     # with two coarse probes the query reaches the next coarse partition
     top2, _ = oracle.multilevel_select(Qe[:1], C, C2e, off2e, ids2e, 5, 2)
     assert np.all(top2[0] >= 0)
+
+
+# ---------------------------------------------------------------- product quantization
+
+def _lattice_index(seed=41, n=600, d=8, c=6, s=1):
+    """Centroids and points with entries in {0, 1}: every residual x - C_p of
+    every copy has entries in {-1, 0, 1}, so each 2-D residual subvector is
+    one of 9 lattice points, which 16 PQ centres represent exactly."""
+    rng = np.random.default_rng(seed)
+    C = rng.integers(0, 2, size=(c, d)).astype(np.float32)
+    X = rng.integers(0, 2, size=(n, d)).astype(np.float32)
+    Q = rng.standard_normal((12, d)).astype(np.float32)
+    A = oracle.soar_assign(X, C, 1.0, s)
+    off, ids = oracle.build_ivf(A, c)
+    return X, Q, C, A, off, ids
+
+
+def _lattice_codebook(d):
+    pts = np.array([[a, b] for a in (-1.0, 0.0, 1.0) for b in (-1.0, 0.0, 1.0)], dtype=np.float32)
+    far = np.array([[50.0 + j, -50.0] for j in range(7)], dtype=np.float32)
+    return np.stack([np.vstack([pts, far]) for _ in range(d // 2)])
+
+
+def test_pq_train_recovers_lattice_centres_and_codes_reconstruct():
+    # residuals whose subvectors take 9 values: started from rows holding all
+    # 9 (plus 7 repeats), k-means ends with the 9 values among its centres,
+    # and every residual is reconstructed exactly by its code
+    X, Q, C, A, off, ids = _lattice_index()
+    part = np.repeat(np.arange(C.shape[0]), np.diff(off))
+    R = oracle.pq_residuals(X[ids], C, part)
+    rng = np.random.default_rng(42)
+    R = np.vstack([np.tile(_lattice_codebook(8)[0][:9].reshape(9, 2), (1, 4)), R])   # rows 0..8: the 9 values
+    init = np.r_[np.arange(9), rng.choice(np.arange(9, R.shape[0]), 7, replace=False)]
+    B = oracle.pq_train(R, 5, init)
+    codes = oracle.pq_encode(R, B)
+    rec = np.stack([B[s][codes[:, s]] for s in range(4)], axis=1).reshape(R.shape)
+    np.testing.assert_array_equal(rec, R)
+
+
+def test_pq_encode_by_loops_with_ties():
+    rng = np.random.default_rng(43)
+    R = rng.standard_normal((30, 6)).astype(np.float32)
+    B = rng.standard_normal((3, 16, 2)).astype(np.float32)
+    B[1, 9] = B[1, 4]                                  # a tied pair of centres: the lower index wins
+    R[5, 2:4] = B[1, 4]
+    codes = oracle.pq_encode(R, B)
+    for i in range(30):
+        for s in range(3):
+            dist = [sum((float(R[i, 2 * s + e]) - float(B[s, j, e])) ** 2 for e in range(2)) for j in range(16)]
+            assert codes[i, s] == min(range(16), key=lambda j: (dist[j], j))
+    assert codes[5, 1] == 4
+
+
+@pytest.mark.parametrize("t", [1, 3, 6])
+def test_pq_search_with_exact_codes_is_ivf_search(t):
+    # exact reconstruction: <q, C_p> + sum <q_s, B[code_s]> = <q, x> for
+    # every copy, so the best k approximate scores are the best k exact ones
+    X, Q, C, A, off, ids = _lattice_index(s=1)
+    B = _lattice_codebook(X.shape[1])
+    codes = oracle.pq_index_codes(X, C, off, ids, B)
+    gi, gs = oracle.pq_search(Q, X, C, off, ids, B, codes, 10, t, 10)
+    wi, ws = oracle.ivf_search(Q, X, C, off, ids, 10, t)
+    np.testing.assert_allclose(gs, ws, rtol=1e-12)
+    exact = X.astype(np.float64) @ Q.astype(np.float64).T
+    for q in range(Q.shape[0]):                        # equal ids up to exact ties on the lattice
+        for a, b in zip(gi[q], wi[q]):
+            assert a == b or exact[a, q] == exact[b, q]
+
+
+def _pq_search_by_loops(q, X, C, off, ids, B, codes, k, t, R):
+    dot = lambda u, v: sum(float(a) * float(b) for a, b in zip(u, v))
+    cs = [dot(q, C[p]) for p in range(len(C))]
+    probes = sorted(range(len(C)), key=lambda p: (-cs[p], p))[:t]
+    approx = {}
+    for p in probes:                                   # earliest probe first
+        for r in range(off[p], off[p + 1]):
+            pid = int(ids[r])
+            if pid in approx:
+                continue
+            approx[pid] = cs[p] + sum(dot(q[2 * s:2 * s + 2], B[s, codes[r, s]]) for s in range(B.shape[0]))
+    short = sorted(approx, key=lambda i: (-approx[i], i))[:R]
+    ex = {i: dot(q, X[i]) for i in short}
+    best = sorted(short, key=lambda i: (-ex[i], i))[:k]
+    return best + [-1] * (k - len(best))
+
+
+@pytest.mark.parametrize("k,t,R", [(5, 2, 12), (3, 3, 3), (10, 1, 40)])
+def test_pq_search_by_loops(k, t, R):
+    # trained (lossy) codes: the shortlist, the earliest-probe rule for a
+    # spilled point's two codes and the exact rescoring, written out by loops
+    rng = np.random.default_rng(44)
+    X = rng.standard_normal((200, 6)).astype(np.float32)
+    Q = rng.standard_normal((5, 6)).astype(np.float32)
+    C = oracle.kmeans(X, rng.choice(200, 8, replace=False), 3)
+    A = oracle.soar_assign(X, C, 1.0, 1)
+    off, ids = oracle.build_ivf(A, 8)
+    part = np.repeat(np.arange(8), np.diff(off))
+    Rres = oracle.pq_residuals(X[ids], C, part)
+    B = oracle.pq_train(Rres, 3, rng.choice(Rres.shape[0], 16, replace=False))
+    codes = oracle.pq_index_codes(X, C, off, ids, B)
+    gi, _ = oracle.pq_search(Q, X, C, off, ids, B, codes, k, t, R)
+    for q in range(5):
+        assert list(gi[q]) == _pq_search_by_loops(Q[q], X, C, off, ids, B, codes, k, t, R)
+
+
+def test_pq_search_rescoring_everything_is_brute_force():
+    X, Q, C, A, off, ids = _small_index()
+    part = np.repeat(np.arange(C.shape[0]), np.diff(off))
+    Rres = oracle.pq_residuals(X[ids], C, part)
+    B = oracle.pq_train(Rres, 2, np.arange(16))
+    codes = oracle.pq_index_codes(X, C, off, ids, B)
+    gi, gs = oracle.pq_search(Q, X, C, off, ids, B, codes, 10, C.shape[0], X.shape[0])
+    wi, ws = oracle.mips_topk(Q, X, 10)
+    np.testing.assert_array_equal(gi, wi)
+    np.testing.assert_allclose(gs, ws, rtol=1e-12)
