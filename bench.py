@@ -648,7 +648,7 @@ def precision_at_size(sb, dev, steps, warmup, n_train=1_000_000, n_test=10_000, 
                                 "qps": n_test / (ms8 / 1e3), "build_ms": build8_ms,
                                 "index_bytes": int(ix8.info.device_bytes),
                                 "bf16_index_bytes": int(ix.info.device_bytes),
-                                "path": "SIMT FP8 scan, per-partition top-rescore lists, exact fp32 rescoring"}
+                                "path": "FP8 scores of each query's probed union (a warp per query, each point once), exact top-rescore shortlist by radix select, exact fp32 rescoring"}
     else:
         fixed["fp8_rescore"] = {"t": None, "recall_at_64": rec8, "rescore": rescore}
     ix8.close()
