@@ -68,7 +68,7 @@ def parse_args():
     p.add_argument("--no-at-size", action="store_true",
                    help="skip the precision (10^7 points), serving (10^8 points) and multi-level (10^5 "
                         "partitions) workloads at full size")
-    p.add_argument("--leg", choices=["precision", "serving", "multilevel"], default=None,
+    p.add_argument("--leg", choices=["precision", "serving", "multilevel", "layouts"], default=None,
                    help="run one full-size workload alone and print its results")
     p.add_argument("--arms", choices=["all", "main"], default="all",
                    help="all: SOAR at lambda 0.5/1/2, spill without SOAR, no spill; main: the timed arm only")
@@ -565,6 +565,68 @@ def spills_study(sb, X, C, Q, truth, k, max_spills=3, targets=(0.8, 0.9, 0.95)):
     return {"lambda": 1.0, "rows": out}
 
 
+def compressed_layouts(sb, X, C, Q, truth, k, steps, warmup, A1=None, train_rows=65_536, pq_iters=10,
+                       rescores=(100, 400)):
+    """Section 3.5's layout (the compressed form duplicated for every
+    assignment, the full-precision rows stored once) on the Glove-shaped
+    SOAR index (lambda = 1): 4-bit PQ codes of every copy's residual (2
+    dimensions, 16 centres per subspace, trained on the residuals of the
+    first 65 536 points, App. A.3) and per-row scaled FP8 codes, each
+    shortlisting `rescore` candidates of the probed union for exact
+    rescoring, against the full fp32 layout scanned exactly.  Per layout: the
+    smallest t reaching recall@10 >= 0.9, time per batch, QPS and device
+    bytes, with and without the spill (SOAR's memory overhead, the analogue
+    of the paper's memory table)."""
+    import torch
+    dev = X.device
+    nq = Q.shape[0]
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        ts = []
+        for i in range(steps):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.mean(ts)
+
+    A1 = A1 if A1 is not None else sb.soar_assign(X, C, 1.0, 1)
+    A0 = A1[:, :1].contiguous()
+    init = torch.from_numpy(synth.init_indices(train_rows, 16, 207)).to(dev)
+    B = sb.soar_pq_train(X[:train_rows], C, A1[:train_rows, 0].contiguous(), pq_iters, init)
+    out = {"pq": {"train_rows": train_rows, "iters": pq_iters, "subspace_dims": 2, "centres": 16}, "layouts": []}
+    builders = {"fp32 exact": lambda A: sb.soar_index_build(X, C, A),
+                "fp8 + rescore": lambda A: sb.soar_index_build(X, C, A, mode=sb.SOAR_SCORE_FP8),
+                "pq4 + rescore": lambda A: sb.soar_index_build_pq(X, C, A, B)}
+    for name, build in builders.items():
+        ix0 = build(A0)
+        bytes0 = int(ix0.info.device_bytes)
+        ix0.close()
+        ix = build(A1)
+        row = {"layout": name, "index_bytes_spill1": int(ix.info.device_bytes), "index_bytes_spill0": bytes0,
+               "soar_overhead": int(ix.info.device_bytes) / bytes0 - 1.0, "points": []}
+        for R in ((None,) if name == "fp32 exact" else rescores):
+            search = (lambda t: sb.soar_search(ix, Q, k, t)[0]) if R is None else \
+                     (lambda t, R=R: sb.soar_search(ix, Q, k, t, rescore=R)[0])
+            t_at, rec = find_t(sb, ix, Q, truth, k, 128, search=search)
+            pt = {"rescore": R, "t": t_at, "recall": rec}
+            if t_at is not None:
+                ms = timed(lambda: search(t_at))
+                pt.update({"ms_per_batch": ms, "qps": nq / (ms / 1e3)})
+            row["points"].append(pt)
+        ix.close()
+        out["layouts"].append(row)
+        log(f"[bench] layout: {row}")
+    return out
+
+
 def precision_at_size(sb, dev, steps, warmup, n_train=1_000_000, n_test=10_000, n_cal=4000, train_rows=1_000_000,
                       batch=50_000):
     """The precision workload at its full size (n = 10^7 unit vectors, d = 96,
@@ -970,6 +1032,10 @@ def run_ours(args):
                 extras["size_study"] = size_study(sb, dev, Xd, Qd[:2000], k)
             except Exception as e:
                 extras["size_study"] = {"error": str(e)[:200]}
+            try:
+                extras["compressed_layouts"] = compressed_layouts(sb, Xd, C, Qd, truth, k, args.steps, args.warmup)
+            except Exception as e:
+                extras["compressed_layouts"] = {"error": str(e)[:200]}
 
     # ---- CPU oracle baseline (rank 0 only, N = 1 only)
     cpu = None
@@ -1033,6 +1099,17 @@ def run_ours(args):
     return 0
 
 
+def glove_layouts(sb, dev, steps, warmup):
+    """``compressed_layouts`` on the Glove-shaped workload built as the main run builds it."""
+    import torch
+    w = synth.WORKLOADS["glove"]
+    X, Q, init = synth.workload_arrays("glove")
+    Xd, Qd = torch.from_numpy(X).to(dev), torch.from_numpy(Q).to(dev)
+    C = sb.soar_train_centroids(Xd, w.c, w.kmeans_iters, torch.from_numpy(init).to(dev))
+    truth = sb.soar_exact_mips(Xd, Qd, w.k)[0]
+    return compressed_layouts(sb, Xd, C, Qd, truth, w.k, steps, warmup)
+
+
 def run_leg(args):
     """One full-size leg alone (its own index), printed as one JSON object."""
     import torch
@@ -1041,7 +1118,8 @@ def run_leg(args):
     dev = torch.device("cuda", 0)
     legs = {"precision": lambda: precision_at_size(sb, dev, args.steps, args.warmup),
             "serving": lambda: serving_at_size(sb, dev),
-            "multilevel": lambda: multilevel_at_size(sb, dev, args.steps, args.warmup)}
+            "multilevel": lambda: multilevel_at_size(sb, dev, args.steps, args.warmup),
+            "layouts": lambda: glove_layouts(sb, dev, args.steps, args.warmup)}
     print(json.dumps({args.leg: legs[args.leg]()}), flush=True)
     return 0
 

@@ -69,8 +69,14 @@ typedef enum { SOAR_F32 = 0, SOAR_BF16 = 1 } soar_dtype;
  *   the exact fp32 rescoring of the best `rescore` candidates.  This is the
  *   GPU analogue of the paper's layout in Section 3.5: only the compressed
  *   representation is duplicated, the highest-bitrate copy is stored once.
+ * SOAR_SCORE_PQ4: every copy holds a 4-bit product-quantization code of its
+ *   partitioning residual x - C_p (2 dimensions and 16 centres per subspace,
+ *   Section 3.5 and App. A.3); the approximate score of a copy is
+ *   <q, C_p> + sum_s <q_s, B_s[code_s]>; the original vectors are stored once
+ *   and rescore the best `rescore` candidates exactly.  Built with
+ *   soar_index_build_pq.
  */
-typedef enum { SOAR_SCORE_F32 = 0, SOAR_SCORE_BF16 = 1, SOAR_SCORE_FP8 = 2 } soar_score_mode;
+typedef enum { SOAR_SCORE_F32 = 0, SOAR_SCORE_BF16 = 1, SOAR_SCORE_FP8 = 2, SOAR_SCORE_PQ4 = 3 } soar_score_mode;
 
 typedef struct soar_index soar_index;   /* opaque; owns its device memory */
 
@@ -196,8 +202,10 @@ SOAR_API soar_status soar_select_partitions(const soar_index* index, const void*
  *   t           partitions probed per query (1 <= t <= min(c, 8192))
  *   t_per_query [nq] int32 per-query probe counts in [0, t] (values outside are
  *               clamped; 0 probes nothing and gives only padding), or NULL for t everywhere
- *   rescore     SOAR_SCORE_FP8 indices: candidates kept per query for exact fp32
- *               rescoring (k <= rescore <= 4096); ignored (pass 0) for SOAR_SCORE_F32
+ *   rescore     SOAR_SCORE_FP8 and SOAR_SCORE_PQ4 indices: candidates kept per query
+ *               (the best approximate scores of the probed union, each point once)
+ *               for exact fp32 rescoring (k <= rescore <= 4096); ignored (pass 0)
+ *               for SOAR_SCORE_F32
  *   ids_out     [nq][k] int64 point ids, scores_out [nq][k] fp32 <q, x>
  * Requires 1 <= k <= 1024.
  */
@@ -281,6 +289,31 @@ SOAR_API soar_status soar_merge_topk(const int64_t* ids, const float* scores, in
 SOAR_API soar_status soar_exact_mips(const void* X, soar_dtype xdtype, int64_t n, int32_t d,
                             const void* Q, soar_dtype qdtype, int64_t nq, int32_t k,
                             int64_t* ids_out, float* scores_out, cudaStream_t stream);
+
+/*
+ * Product-quantization codebooks of the partitioning residuals (Section
+ * 3.5, App. A.3): r = x - C[part[i]] formed in fp32 for the n training rows,
+ * then for every subspace s (dimensions 2s and 2s+1) Lloyd's k-means with 16
+ * centres started from the rows init_idx [16] (distinct, in [0, n), device
+ * int32; the same rows for every subspace), `iters` steps, each centre the
+ * fp64 mean of its rows rounded to fp32 (an empty one keeps its value).
+ *   X [n][d] (dtype), C [c][d] fp32, part [n] int32 in [0, c) (each row's
+ *   primary partition), B_out [d/2][16][2] fp32.  Requires d even.
+ */
+SOAR_API soar_status soar_pq_train(const void* X, soar_dtype dtype, int64_t n, int32_t d, const float* C, int32_t c,
+                                   const int32_t* part, int32_t iters, const int32_t* init_idx, float* B_out,
+                                   cudaStream_t stream);
+
+/*
+ * soar_index_build with mode SOAR_SCORE_PQ4: every copy (point x in
+ * partition p) is encoded from x - C_p with the codebooks B [d/2][16][2]
+ * (per subspace the nearest centre, the lower index on ties), two codes per
+ * byte (the even subspace in the low nibble); the original vectors are
+ * stored once, indexed by id.  Other arguments as soar_index_build.
+ */
+SOAR_API soar_status soar_index_build_pq(const void* X, soar_dtype dtype, int64_t n, int32_t d, const float* C,
+                                         int32_t c, const int32_t* assign, int32_t spills, const float* B,
+                                         soar_index** out, cudaStream_t stream);
 
 /*
  * Per-row FP8-E4M3 quantisation used by SOAR_SCORE_FP8 indices:

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libsoar.so")
 
 SOAR_OK, SOAR_EINVAL, SOAR_ENOMEM, SOAR_ECUDA, SOAR_ETIMEOUT, SOAR_EUNSUPPORTED = range(6)
 SOAR_F32, SOAR_BF16 = 0, 1
-SOAR_SCORE_F32, SOAR_SCORE_BF16, SOAR_SCORE_FP8 = 0, 1, 2
+SOAR_SCORE_F32, SOAR_SCORE_BF16, SOAR_SCORE_FP8, SOAR_SCORE_PQ4 = 0, 1, 2, 3
 STATUS_NAMES = {0: "SOAR_OK", 1: "SOAR_EINVAL", 2: "SOAR_ENOMEM", 3: "SOAR_ECUDA",
                 4: "SOAR_ETIMEOUT", 5: "SOAR_EUNSUPPORTED"}
 
@@ -69,6 +69,8 @@ _SIGS = {
     "soar_merge_topk": ([_P, _P, _I64, _I32, _I32, _P, _I32, _P, _P, _P], _I32),
     "soar_select_partitions_static": ([_P, _P, _I32, _I64, _I32, _P, _P, _P], _I32),
     "soar_index_build_coarse": ([_P, _I32, _I32, _P, _F32, _I32, ct.POINTER(_P), _P], _I32),
+    "soar_pq_train": ([_P, _I32, _I64, _I32, _P, _I32, _P, _I32, _P, _P, _P], _I32),
+    "soar_index_build_pq": ([_P, _I32, _I64, _I32, _P, _I32, _P, _I32, _P, ct.POINTER(_P), _P], _I32),
     "soar_select_partitions_multilevel": ([_P, _P, _I32, _I64, _I32, _I32, _P, _P, _P, _P], _I32),
     "soar_search_multilevel": ([_P, _P, _P, _I32, _I64, _I32, _I32, _I32, _I32, _P, _P, _P], _I32),
     "soar_check_device": ([], _I32),
@@ -206,7 +208,7 @@ class Index:
 
     def vectors(self) -> torch.Tensor:
         i = self.info
-        if i.mode == SOAR_SCORE_FP8:
+        if i.mode in (SOAR_SCORE_FP8, SOAR_SCORE_PQ4):      # byte codes, row_stride bytes per copy
             return self._view(i.vectors, i.rows * i.row_stride, torch.uint8).clone().view(i.rows, i.row_stride)
         dt = torch.float32 if i.dtype == SOAR_F32 else torch.bfloat16
         return self._view(i.vectors, i.rows * i.row_stride, dt).clone().view(i.rows, i.row_stride)
@@ -248,6 +250,29 @@ def soar_index_build(X: torch.Tensor, C: torch.Tensor, assign: torch.Tensor, mod
     _check(load().soar_index_build(_dev(X, "X", ndim=2), _dtype(X), n, d, _dev(C, "C", torch.float32, 2), c,
                                    _dev(assign, "assign", torch.int32, 2), spills, mode, ct.byref(h),
                                    _stream(stream)))
+    return Index(h)
+
+
+def soar_pq_train(X: torch.Tensor, C: torch.Tensor, part: torch.Tensor, iters: int, init_idx: torch.Tensor,
+                  stream=None) -> torch.Tensor:
+    """PQ codebooks [d/2, 16, 2] of the residuals X[i] - C[part[i]]."""
+    n, d = X.shape
+    B = torch.empty((d // 2, 16, 2), dtype=torch.float32, device=X.device)
+    _check(load().soar_pq_train(_dev(X, "X", ndim=2), _dtype(X), n, d, _dev(C, "C", torch.float32, 2), C.shape[0],
+                                _dev(part, "part", torch.int32, 1), iters, _dev(init_idx, "init_idx", torch.int32, 1),
+                                _dev(B, "B"), _stream(stream)))
+    return B
+
+
+def soar_index_build_pq(X: torch.Tensor, C: torch.Tensor, assign: torch.Tensor, B: torch.Tensor,
+                        stream=None) -> Index:
+    n, d = X.shape
+    if assign.shape[0] != n:
+        raise ValueError("assign must have one row per datapoint")
+    h = ct.c_void_p()
+    _check(load().soar_index_build_pq(_dev(X, "X", ndim=2), _dtype(X), n, d, _dev(C, "C", torch.float32, 2),
+                                      C.shape[0], _dev(assign, "assign", torch.int32, 2), assign.shape[1] - 1,
+                                      _dev(B, "B", torch.float32, 3), ct.byref(h), _stream(stream)))
     return Index(h)
 
 

@@ -186,7 +186,9 @@ soar_status soar_index_build(const void* X, soar_dtype dtype, int64_t n, int32_t
     SOAR_REQUIRE(n >= 1 && d >= 1 && d <= 4096 && c >= 1, "bad sizes");
     SOAR_REQUIRE(spills >= 0 && spills <= 4 && c >= 1 + spills, "spills must be in [0, 4] and <= c - 1");
     SOAR_REQUIRE(n * (1 + spills) < (int64_t(1) << 31), "n * (1 + spills) must be < 2^31");
-    SOAR_REQUIRE(mode == SOAR_SCORE_F32 || mode == SOAR_SCORE_FP8 || mode == SOAR_SCORE_BF16, "unknown mode");
+    SOAR_REQUIRE(mode == SOAR_SCORE_F32 || mode == SOAR_SCORE_FP8 || mode == SOAR_SCORE_BF16 ||
+                     mode == SOAR_SCORE_PQ4, "unknown mode");
+    SOAR_REQUIRE(mode != SOAR_SCORE_PQ4, "a SOAR_SCORE_PQ4 index needs its codebooks: use soar_index_build_pq");
     if (mode == SOAR_SCORE_BF16) soar::fail(SOAR_EUNSUPPORTED, "soar_index_build: SOAR_SCORE_BF16 not implemented");
     soar_index* ix = new soar_index;
     ix->data.n = n;
@@ -198,6 +200,51 @@ soar_status soar_index_build(const void* X, soar_dtype dtype, int64_t n, int32_t
     ix->data.rows = n * (1 + spills);
     try {
       soar::build_index(ix->data, X, dtype, C, assign, stream);
+    } catch (...) {
+      cudaStreamSynchronize(stream);
+      soar::free_index(ix->data);
+      delete ix;
+      throw;
+    }
+    *out = ix;
+  });
+}
+
+soar_status soar_pq_train(const void* X, soar_dtype dtype, int64_t n, int32_t d, const float* C, int32_t c,
+                          const int32_t* part, int32_t iters, const int32_t* init_idx, float* B_out,
+                          cudaStream_t stream) {
+  return guarded([&] {
+    SOAR_REQUIRE(X && C && part && init_idx && B_out, "null pointer");
+    SOAR_REQUIRE(valid_dtype(dtype), "unknown dtype");
+    SOAR_REQUIRE(n >= 16 && n < (int64_t(1) << 31), "n must be in [16, 2^31)");
+    SOAR_REQUIRE(d >= 2 && d <= 4096 && d % 2 == 0, "d must be even and in [2, 4096]");
+    SOAR_REQUIRE(c >= 1, "c must be >= 1");
+    SOAR_REQUIRE(iters >= 0, "iters must be >= 0");
+    SOAR_REQUIRE(n * (int64_t)d < (int64_t(1) << 40), "n * d too large");
+    soar::Scratch scr(stream);
+    soar::pq_train(X, dtype, n, d, C, part, iters, init_idx, B_out, stream, scr);
+  });
+}
+
+soar_status soar_index_build_pq(const void* X, soar_dtype dtype, int64_t n, int32_t d, const float* C, int32_t c,
+                                const int32_t* assign, int32_t spills, const float* B, soar_index** out,
+                                cudaStream_t stream) {
+  return guarded([&] {
+    SOAR_REQUIRE(X && C && assign && B && out, "null pointer");
+    SOAR_REQUIRE(valid_dtype(dtype), "unknown dtype");
+    SOAR_REQUIRE(n >= 1 && d >= 2 && d <= 4096 && d % 2 == 0 && c >= 1, "bad sizes (d must be even)");
+    SOAR_REQUIRE(spills >= 0 && spills <= 4 && c >= 1 + spills, "spills must be in [0, 4] and <= c - 1");
+    SOAR_REQUIRE(n * (1 + spills) < (int64_t(1) << 31), "n * (1 + spills) must be < 2^31");
+    soar_index* ix = new soar_index;
+    ix->data.n = n;
+    ix->data.d = d;
+    ix->data.c = c;
+    ix->data.spills = spills;
+    ix->data.mode = SOAR_SCORE_PQ4;
+    ix->data.dtype = dtype;
+    ix->data.rows = n * (1 + spills);
+    try {
+      soar::build_index(ix->data, X, dtype, C, assign, stream, B);
     } catch (...) {
       cudaStreamSynchronize(stream);
       soar::free_index(ix->data);
@@ -284,8 +331,8 @@ soar_status soar_search(const soar_index* index, const void* Q, soar_dtype dtype
     SOAR_REQUIRE(nq >= 1 && nq * (int64_t)t < (int64_t(1) << 31), "nq * t must be in [1, 2^31)");
     SOAR_REQUIRE(k >= 1 && k <= 1024, "k must be in [1, 1024]");
     SOAR_REQUIRE(t >= 1 && t <= index->data.c && t <= 8192, "t must be in [1, min(c, 8192)]");
-    if (index->data.mode == SOAR_SCORE_FP8)
-      SOAR_REQUIRE(rescore >= k && rescore <= 4096, "rescore must be in [k, 4096] for an FP8 index");
+    if (index->data.mode == SOAR_SCORE_FP8 || index->data.mode == SOAR_SCORE_PQ4)
+      SOAR_REQUIRE(rescore >= k && rescore <= 4096, "rescore must be in [k, 4096] for an FP8 or PQ4 index");
     soar::Scratch scr(stream);
     soar::search(index->data, Q, dtype, nq, k, t, t_per_query, rescore, ids_out, scores_out, stream, scr);
   });
@@ -354,8 +401,8 @@ soar_status soar_search_multilevel(const soar_index* index, const soar_index* co
     SOAR_REQUIRE(k >= 1 && k <= 1024, "k must be in [1, 1024]");
     SOAR_REQUIRE(t >= 1 && t <= index->data.c && t <= 1024, "t must be in [1, min(c, 1024)]");
     SOAR_REQUIRE(t1 >= 1 && t1 <= coarse->data.c && t1 <= 8192, "t1 must be in [1, min(c2, 8192)]");
-    if (index->data.mode == SOAR_SCORE_FP8)
-      SOAR_REQUIRE(rescore >= k && rescore <= 4096, "rescore must be in [k, 4096] for an FP8 index");
+    if (index->data.mode == SOAR_SCORE_FP8 || index->data.mode == SOAR_SCORE_PQ4)
+      SOAR_REQUIRE(rescore >= k && rescore <= 4096, "rescore must be in [k, 4096] for an FP8 or PQ4 index");
     soar::Scratch scr(stream);
     soar::search(index->data, Q, dtype, nq, k, t, nullptr, rescore, ids_out, scores_out, stream, scr, &coarse->data,
                  t1);

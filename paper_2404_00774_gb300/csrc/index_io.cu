@@ -3,7 +3,7 @@
 // read), so that a large index is built once.
 //
 // File format (little-endian, no padding between sections):
-//   header   struct FileHeader below (magic "SOARIDX1", format version 1,
+//   header   struct FileHeader below (magic "SOARIDX1", format version 2,
 //            the scalar fields of the index, then the byte size of every
 //            array section in the fixed order of kSections)
 //   arrays   each present array's bytes, in that order
@@ -21,8 +21,8 @@ namespace soar {
 namespace {
 
 constexpr char kMagic[8] = {'S', 'O', 'A', 'R', 'I', 'D', 'X', '1'};
-constexpr uint32_t kVersion = 1;
-constexpr int kSections = 16;
+constexpr uint32_t kVersion = 2;
+constexpr int kSections = 17;
 constexpr size_t kChunk = size_t(64) << 20;
 
 struct FileHeader {
@@ -30,7 +30,7 @@ struct FileHeader {
   uint32_t version;
   uint32_t header_bytes;
   int64_t n, rows, max_partition, tc_groups, bytes;
-  int32_t d, c, spills, mode, dtype, row_stride, code_stride, tc_kp, sel_kp, sel_tiles;
+  int32_t d, c, spills, mode, dtype, row_stride, code_stride, tc_kp, sel_kp, sel_tiles, pq_m, reserved;
   uint64_t section_bytes[kSections];
 };
 
@@ -43,8 +43,8 @@ struct Section {
 
 void sections(IndexData& ix, Section (&out)[kSections]) {
   const size_t esz = ix.dtype == SOAR_F32 ? 4 : 2;
-  const bool fp8 = ix.mode == SOAR_SCORE_FP8;
-  const size_t vec_bytes = fp8 ? (size_t)ix.rows * ix.code_stride : esz * (size_t)ix.rows * ix.row_stride;
+  const bool coded = ix.mode == SOAR_SCORE_FP8 || ix.mode == SOAR_SCORE_PQ4;   // byte codes per copy
+  const size_t vec_bytes = coded ? (size_t)ix.rows * ix.code_stride : esz * (size_t)ix.rows * ix.row_stride;
   const int ostride = (int)(((ix.d * esz + 15) / 16) * 16 / esz);
   int i = 0;
   auto add = [&](void** p, size_t b) { out[i++] = Section{p, b}; };
@@ -64,6 +64,7 @@ void sections(IndexData& ix, Section (&out)[kSections]) {
   add((void**)&ix.tc_pmax, sizeof(float) * ix.c);
   add((void**)&ix.assign, sizeof(int32_t) * (size_t)ix.n * (1 + ix.spills));
   add((void**)&ix.sel_cb, sizeof(float) * 2 * 64 * (size_t)ix.sel_kp * ix.sel_tiles);
+  add((void**)&ix.pq_cb, sizeof(float) * (size_t)ix.pq_m * 16 * 2);
 }
 
 struct File {
@@ -93,6 +94,7 @@ void save_index(const IndexData& ix_in, const char* path, cudaStream_t s) {
   h.n = ix.n; h.rows = ix.rows; h.max_partition = ix.max_partition; h.tc_groups = ix.tc_groups; h.bytes = ix.bytes;
   h.d = ix.d; h.c = ix.c; h.spills = ix.spills; h.mode = ix.mode; h.dtype = ix.dtype; h.row_stride = ix.row_stride;
   h.code_stride = ix.code_stride; h.tc_kp = ix.tc_kp; h.sel_kp = ix.sel_kp; h.sel_tiles = ix.sel_tiles;
+  h.pq_m = ix.pq_m;
   for (int i = 0; i < kSections; ++i) h.section_bytes[i] = *sec[i].ptr ? sec[i].bytes : 0;
   File f;
   f.f = fopen(path, "wb");
@@ -123,12 +125,14 @@ void load_index(IndexData& ix, const char* path, cudaStream_t s) {
     fail(SOAR_EUNSUPPORTED, "soar_index_load: unsupported format version");
   const bool sane = h.n >= 1 && h.d >= 1 && h.d <= 4096 && h.c >= 1 && h.spills >= 0 && h.spills <= 4 &&
                     h.rows == h.n * (1 + h.spills) &&
-                    (h.mode == SOAR_SCORE_F32 || h.mode == SOAR_SCORE_FP8) &&
+                    (h.mode == SOAR_SCORE_F32 || h.mode == SOAR_SCORE_FP8 || h.mode == SOAR_SCORE_PQ4) &&
+                    (h.mode == SOAR_SCORE_PQ4 ? h.pq_m == h.d / 2 : h.pq_m == 0) &&
                     (h.dtype == SOAR_F32 || h.dtype == SOAR_BF16);
   if (!sane) fail(SOAR_EINVAL, "soar_index_load: header fields out of range");
   ix.n = h.n; ix.rows = h.rows; ix.max_partition = h.max_partition; ix.tc_groups = h.tc_groups;
   ix.d = h.d; ix.c = h.c; ix.spills = h.spills; ix.mode = h.mode; ix.dtype = h.dtype; ix.row_stride = h.row_stride;
   ix.code_stride = h.code_stride; ix.tc_kp = h.tc_kp; ix.sel_kp = h.sel_kp; ix.sel_tiles = h.sel_tiles;
+  ix.pq_m = h.pq_m;
   // every section the file carries must have the size the header's fields
   // give it; the offsets, ids, vectors and centroids must be present
   Section sec[kSections];
@@ -136,7 +140,7 @@ void load_index(IndexData& ix, const char* path, cudaStream_t s) {
   for (int i = 0; i < kSections; ++i) {
     if (h.section_bytes[i] != 0 && h.section_bytes[i] != sec[i].bytes)
       fail(SOAR_EINVAL, "soar_index_load: section " + std::to_string(i) + " has the wrong size");
-    if (h.section_bytes[i] == 0 && (i == 0 || i == 1 || i == 2 || i == 5))
+    if (h.section_bytes[i] == 0 && (i == 0 || i == 1 || i == 2 || i == 5 || (i == 16 && h.mode == SOAR_SCORE_PQ4)))
       fail(SOAR_EINVAL, "soar_index_load: a required section is missing");
   }
   for (int i = 0; i < kSections; ++i) {

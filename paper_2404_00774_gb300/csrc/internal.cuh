@@ -78,6 +78,10 @@ struct IndexData {
   // core-matrix layout (K = sel_kp); null when that kernel does not apply
   float* sel_cb = nullptr;
   int32_t sel_kp = 0, sel_tiles = 0;
+  // PQ4 indexes: codebooks [pq_m][16][2] of the residuals; the codes of every
+  // copy are `vectors` ([rows][code_stride] bytes, two 4-bit codes a byte)
+  float* pq_cb = nullptr;
+  int32_t pq_m = 0;
 };
 
 }  // namespace soar
@@ -90,7 +94,13 @@ struct soar_index {
 namespace soar {
 
 void build_index(IndexData& ix, const void* X, soar_dtype dt, const float* C, const int32_t* assign,
-                 cudaStream_t s);
+                 cudaStream_t s, const float* pq_cb = nullptr);
+
+// PQ codebooks B [d/2][16][2] of the residuals X[i] - C[part[i]] (pq.cu).
+void pq_train(const void* X, soar_dtype dt, int64_t n, int32_t d, const float* C, const int32_t* part,
+              int32_t iters, const int32_t* init_idx, float* B, cudaStream_t s, Scratch& scr);
+// Codes of every index row from its residual x - C_p (pq.cu).
+void pq_encode_index(IndexData& ix, const void* X, soar_dtype dt, cudaStream_t s, Scratch& scr);
 void free_index(IndexData& ix);
 
 // A flat index over fx.n rows (fx.vectors, fx.dtype, fx.row_stride, fx.d and

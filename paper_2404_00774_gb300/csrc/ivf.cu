@@ -215,7 +215,7 @@ void quantize_fp8(const void* V, soar_dtype dt, int64_t m, int32_t d, uint8_t* c
 // Builds every device array of the index; synchronises `s` once to read the
 // validity flag and the partition sizes.
 void build_index(IndexData& ix, const void* X, soar_dtype dt, const float* C, const int32_t* assign,
-                 cudaStream_t s) {
+                 cudaStream_t s, const float* pq_cb) {
   Scratch scr(s);
   const int a = 1 + ix.spills;
   const int64_t n = ix.n, rows = ix.rows;
@@ -290,6 +290,25 @@ void build_index(IndexData& ix, const void* X, soar_dtype dt, const float* C, co
     decode_codes<<<ceil_div((int64_t)c * ix.code_stride, 256), 256, 0, s>>>(ccodes, (int64_t)c * ix.code_stride,
                                                                           ix.cent_code_vals);
     SOAR_LAUNCHED();
+  } else if (ix.mode == SOAR_SCORE_PQ4) {
+    // two 4-bit codes per byte, rows padded to 16 bytes; the originals once
+    ix.pq_m = d / 2;
+    ix.code_stride = ((ix.pq_m + 1) / 2 + 15) / 16 * 16;
+    ix.row_stride = ix.code_stride;
+    dev_alloc(&ix.vectors, (size_t)rows * ix.code_stride);
+    dev_alloc((void**)&ix.pq_cb, sizeof(float) * (size_t)ix.pq_m * 16 * 2);
+    SOAR_CUDA(cudaMemcpyAsync(ix.pq_cb, pq_cb, sizeof(float) * (size_t)ix.pq_m * 16 * 2, cudaMemcpyDeviceToDevice,
+                              s));
+    const int ostride = (int)(((d * esz + 15) / 16) * 16 / esz);
+    dev_alloc(&ix.originals, esz * (size_t)n * ostride);
+    if (dt == SOAR_F32)
+      gather_rows<float><<<(unsigned)n, 128, 0, s>>>(static_cast<const float*>(X), d, nullptr, n, ostride,
+                                                     static_cast<float*>(ix.originals));
+    else
+      gather_rows<__nv_bfloat16><<<(unsigned)n, 128, 0, s>>>(static_cast<const __nv_bfloat16*>(X), d, nullptr, n,
+                                                             ostride, static_cast<__nv_bfloat16*>(ix.originals));
+    SOAR_LAUNCHED();
+    pq_encode_index(ix, X, dt, s, scr);
   } else {
     fail(SOAR_EUNSUPPORTED, "soar_index_build: SOAR_SCORE_BF16 is not implemented");
   }
@@ -367,7 +386,7 @@ void build_index(IndexData& ix, const void* X, soar_dtype dt, const float* C, co
 void free_index(IndexData& ix) {
   void* ptrs[] = {ix.offsets, ix.ids, ix.vectors, ix.row_scales, ix.originals, ix.centroids,
                   ix.part_order, ix.cent_code_vals, ix.cent_scales, ix.tc_rows, ix.tc_gstart,
-                  ix.tc_ids, ix.tc_norms, ix.tc_pmax, ix.assign, ix.sel_cb};
+                  ix.tc_ids, ix.tc_norms, ix.tc_pmax, ix.assign, ix.sel_cb, ix.pq_cb};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   ix = IndexData{};

@@ -98,5 +98,10 @@ void scan_by_query(const IndexData& ix, const float* Qf, int qstride, const int3
 // the queries' code values (code_stride columns), qscale their scales.
 void fp8_shortlist(const IndexData& ix, const float* Qf, const float* qscale, const int32_t* top,
                    const int32_t* tpq, int64_t nq, int t, int R, int32_t* cand, cudaStream_t s, Scratch& scr);
+// The same shortlist for a PQ4 index: approximate score <q, C_p> + sum_s
+// <q_s, B[s][code_s]> of each point's earliest-probed copy; Qf fp32 rows of
+// qstride columns.
+void pq_shortlist(const IndexData& ix, const float* Qf, int qstride, const int32_t* top, const int32_t* tpq,
+                  int64_t nq, int t, int R, int32_t* cand, cudaStream_t s, Scratch& scr);
 
 }  // namespace soar

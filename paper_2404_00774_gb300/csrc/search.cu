@@ -1068,11 +1068,13 @@ void search(const IndexData& ix, const void* Q, soar_dtype dt, int64_t nq, int32
     stage_mark(s, "merge", false);
     return;
   }
-  // query rows padded exactly like the index rows (float elements)
+  // query rows padded exactly like the index rows (float elements); a PQ4
+  // index scores fp32 query rows against fp32 centroids and its LUTs
+  const bool pq = ix.mode == SOAR_SCORE_PQ4;
   int qstride;
   if (fp8) qstride = ix.code_stride;
-  else if (ix.dtype == SOAR_F32) qstride = ix.row_stride;
-  else qstride = ix.row_stride;            // bf16 rows: row_stride elements
+  else if (pq) qstride = (ix.d + 3) / 4 * 4;
+  else qstride = ix.row_stride;            // fp32 or bf16 rows: row_stride elements
   float* Qf = scr.get<float>((size_t)nq * qstride);
   float* qscale = fp8 ? scr.get<float>(nq) : nullptr;
   stage_mark(s, "select", true);
@@ -1086,7 +1088,7 @@ void search(const IndexData& ix, const void* Q, soar_dtype dt, int64_t nq, int32
     select_prepared(ix, Qf, qscale, nq, qstride, t, top, nullptr, s, scr);
   }
   stage_mark(s, "select", false);
-  if (!fp8) {
+  if (!fp8 && !pq) {
     const int64_t P = nq * t;
     int32_t* inv = scr.get<int32_t>(P);
     Cand* partials = scr.get<Cand>((size_t)P * k);
@@ -1103,11 +1105,14 @@ void search(const IndexData& ix, const void* Q, soar_dtype dt, int64_t nq, int32
     stage_mark(s, "merge", false);
     return;
   }
-  // FP8: the best `rescore` approximate scores of each query's probed union
-  // (each point once), rescored exactly in fp32 from the stored rows.
+  // FP8 / PQ4: the best `rescore` approximate scores of each query's probed
+  // union (each point once), rescored exactly in fp32 from the stored rows.
   int32_t* cand = scr.get<int32_t>((size_t)nq * rescore);
   stage_mark(s, "scan", true);
-  fp8_shortlist(ix, Qf, qscale, top, tpq, nq, t, rescore, cand, s, scr);
+  if (fp8)
+    fp8_shortlist(ix, Qf, qscale, top, tpq, nq, t, rescore, cand, s, scr);
+  else
+    pq_shortlist(ix, Qf, qstride, top, tpq, nq, t, rescore, cand, s, scr);
   stage_mark(s, "scan", false);
   float* work = scr.get<float>((size_t)nq * rescore);
   const int ostride = ix.dtype == SOAR_F32 ? (ix.d + 3) / 4 * 4 : (ix.d + 7) / 8 * 8;

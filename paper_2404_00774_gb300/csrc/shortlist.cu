@@ -1,8 +1,10 @@
 // Exact top-R shortlist of approximately scored candidates over each query's
 // probed union (Section 3.5: compressed representations are duplicated for
 // every assignment, the high-bitrate rows are stored once and rescore the
-// best candidates), for the FP8 layout: per-row scaled E4M3 codes of every
-// copy, approximate score s_q * s_x * sum q8 x8.
+// best candidates), for two compressed layouts: per-row scaled E4M3 codes
+// of every copy (approximate score s_q * s_x * sum q8 x8), and 4-bit PQ
+// codes of every copy's residual x - C_p (approximate score <q, C_p> +
+// sum_s <q_s, B[s][code_s]>).
 //
 // Two kernels, a warp per query:
 //   approx_union  walks the query's probed partitions (lane = row, code rows
@@ -32,22 +34,97 @@ __device__ __forceinline__ float fp8_code_value(uint32_t b) {
   return __half2float(__half(h));
 }
 
-__global__ void __launch_bounds__(32 * kSlWarps) approx_union_fp8(
-    const uint8_t* __restrict__ codes, int code_stride, const float* __restrict__ row_scales,
-    const int32_t* __restrict__ ids, const int64_t* __restrict__ off, const int32_t* __restrict__ assign, int a,
-    const float* __restrict__ Qf, const float* __restrict__ qscale, const int32_t* __restrict__ top,
-    const int32_t* __restrict__ tpq, int64_t q0, int64_t nq, int t, int64_t slice, uint64_t* __restrict__ keys,
-    int64_t* __restrict__ counts) {
+// FP8 rows: approx = s_q * s_x * sum q8 x8 (products summed in fp32 in
+// ascending element order); per warp the query's code values.
+struct Fp8Rows {
+  const uint8_t* codes;
+  int code_stride;
+  const float* row_scales;
+  const float* Qf;        // [nq][code_stride] code values
+  const float* qscale;
+  __host__ __device__ int smem_floats() const { return code_stride; }
+  __device__ void load(float* qs, int64_t q, int lane) const {
+    for (int i = lane; i < code_stride; i += 32) qs[i] = Qf[q * (int64_t)code_stride + i];
+  }
+  __device__ float partition_base(const float*, int, int) const { return 0.f; }
+  __device__ float score(const float* qs, int64_t q, int64_t r, float) const {
+    const uint4* x = reinterpret_cast<const uint4*>(codes + r * (int64_t)code_stride);
+    float acc = 0.f;
+    for (int c = 0; c < code_stride / 16; ++c) {
+      const uint4 v = __ldg(x + c);
+      const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc = fmaf(qs[16 * c + 4 * i + b], fp8_code_value((wv[i] >> (8 * b)) & 0xffu), acc);
+    }
+    return acc * qscale[q] * row_scales[r];
+  }
+};
+
+// PQ4 rows: approx = <q, C_p> + sum_s LUT[s][code_s] with LUT[s][j] =
+// <q_s, B[s][j]>; per warp the LUT ([m][16]) followed by the query row.
+struct Pq4Rows {
+  const uint8_t* codes;
+  int code_stride, m, d;
+  const float* B;         // [m][16][2]
+  const float* C;         // [c][d]
+  const float* Qf;        // [nq][qstride] fp32
+  int qstride;
+  __host__ __device__ int smem_floats() const { return m * 16 + qstride; }
+  __device__ void load(float* qs, int64_t q, int lane) const {
+    float* qrow = qs + m * 16;
+    for (int i = lane; i < qstride; i += 32) qrow[i] = Qf[q * (int64_t)qstride + i];
+    for (int e = lane; e < m * 16; e += 32) {
+      const int sidx = e / 16;
+      const float q0 = Qf[q * (int64_t)qstride + 2 * sidx], q1 = Qf[q * (int64_t)qstride + 2 * sidx + 1];
+      qs[e] = fmaf(q1, B[2 * e + 1], q0 * B[2 * e]);
+    }
+  }
+  // <q, C_p> in fp32 (lanes over the dimensions, a fixed shuffle tree, lane 0's value to all)
+  __device__ float partition_base(const float* qs, int p, int lane) const {
+    const float* qrow = qs + m * 16;
+    const float* cp = C + (int64_t)p * d;
+    float v = 0.f;
+    for (int k = lane; k < d; k += 32) v = fmaf(qrow[k], cp[k], v);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return __shfl_sync(0xffffffffu, v, 0);
+  }
+  __device__ float score(const float* qs, int64_t, int64_t r, float base) const {
+    const uint4* x = reinterpret_cast<const uint4*>(codes + r * (int64_t)code_stride);
+    float acc = 0.f;
+    for (int c = 0; c < code_stride / 16; ++c) {
+      const uint4 v = __ldg(x + c);
+      const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+          const int sidx = 32 * c + 8 * i + b;        // nibble b of word i of chunk c
+          if (sidx < m) acc += qs[16 * sidx + ((wv[i] >> (4 * b)) & 0xfu)];
+        }
+    }
+    return base + acc;
+  }
+};
+
+template <typename Rows>
+__global__ void __launch_bounds__(32 * kSlWarps) approx_union(
+    Rows rows, const int32_t* __restrict__ ids, const int64_t* __restrict__ off, const int32_t* __restrict__ assign,
+    int a, const int32_t* __restrict__ top, const int32_t* __restrict__ tpq, int64_t q0, int64_t nq, int t,
+    int64_t slice, uint64_t* __restrict__ keys, int64_t* __restrict__ counts) {
   constexpr unsigned kFull = 0xffffffffu;
   extern __shared__ __align__(16) unsigned char sl_smem[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t ql = (int64_t)blockIdx.x * kSlWarps + w;   // query within this chunk
   if (ql >= nq) return;                                   // uniform within the warp
   const int64_t q = q0 + ql;
-  float* qs = reinterpret_cast<float*>(sl_smem) + w * code_stride;
-  int32_t* probes_s = reinterpret_cast<int32_t*>(reinterpret_cast<float*>(sl_smem) + kSlWarps * code_stride) +
+  const int per = rows.smem_floats();
+  float* qs = reinterpret_cast<float*>(sl_smem) + w * per;
+  int32_t* probes_s = reinterpret_cast<int32_t*>(reinterpret_cast<float*>(sl_smem) + kSlWarps * per) +
                       w * kSlMaxProbesSmem;
-  for (int i = lane; i < code_stride; i += 32) qs[i] = Qf[q * (int64_t)code_stride + i];
+  rows.load(qs, q, lane);
   const int tq = tpq ? min(max(tpq[q], 0), t) : t;
   const int32_t* probes = top + q * (int64_t)t;
   if (t <= kSlMaxProbesSmem) {
@@ -55,11 +132,11 @@ __global__ void __launch_bounds__(32 * kSlWarps) approx_union_fp8(
     probes = probes_s;
   }
   __syncwarp();
-  const float qsc = qscale[q];
   uint64_t* out = keys + ql * slice;
   int64_t n = 0;
   for (int j = 0; j < tq; ++j) {
     const int p = probes[j];
+    const float base = rows.partition_base(qs, p, lane);
     const int64_t r0 = off[p], r1 = off[p + 1];
     for (int64_t rb = r0; rb < r1; rb += 32) {
       const int64_t r = rb + lane;
@@ -75,19 +152,7 @@ __global__ void __launch_bounds__(32 * kSlWarps) approx_union_fp8(
           for (int jj = 0; jj < j; ++jj)
             if (probes[jj] == other) { keep = false; break; }
         }
-        if (keep) {
-          const uint4* x = reinterpret_cast<const uint4*>(codes + r * (int64_t)code_stride);
-          float acc = 0.f;
-          for (int c = 0; c < code_stride / 16; ++c) {
-            const uint4 v = __ldg(x + c);
-            const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-              for (int b = 0; b < 4; ++b) acc = fmaf(qs[16 * c + 4 * i + b], fp8_code_value((wv[i] >> (8 * b)) & 0xffu), acc);
-          }
-          key = rank_key(acc * qsc * row_scales[r], (uint32_t)id);
-        }
+        if (keep) key = rank_key(rows.score(qs, q, r, base), (uint32_t)id);
       }
       const unsigned bal = __ballot_sync(kFull, keep);
       if (keep) out[n + __popc(bal & ((1u << lane) - 1u))] = key;
@@ -171,28 +236,42 @@ __global__ void __launch_bounds__(32 * kSlWarps) select_top_r(const uint64_t* __
   for (int64_t i = min(m, (int64_t)R) + lane; i < R; i += 32) out[i] = -1;
 }
 
-}  // namespace
 
-void fp8_shortlist(const IndexData& ix, const float* Qf, const float* qscale, const int32_t* top,
-                   const int32_t* tpq, int64_t nq, int t, int R, int32_t* cand, cudaStream_t s, Scratch& scr) {
+template <typename Rows>
+void run_shortlist(const IndexData& ix, const Rows& rws, const int32_t* top, const int32_t* tpq, int64_t nq, int t,
+                   int R, int32_t* cand, cudaStream_t s, Scratch& scr) {
   const int64_t slice = std::max<int64_t>(1, std::min<int64_t>((int64_t)t * ix.max_partition, ix.rows));
   // queries per pass so that the key buffer stays within 2 GB
   const int64_t chunk = std::max<int64_t>(kSlWarps, std::min<int64_t>(nq, ((int64_t)1 << 28) / slice));
   const int64_t cq = std::min(chunk, nq);
   uint64_t* keys = scr.get<uint64_t>((size_t)cq * slice);
   int64_t* counts = scr.get<int64_t>(cq);
-  const size_t smem = (size_t)kSlWarps * ix.code_stride * sizeof(float) + (size_t)kSlWarps * kSlMaxProbesSmem * 4;
-  SOAR_CUDA(cudaFuncSetAttribute(approx_union_fp8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const size_t smem = (size_t)kSlWarps * rws.smem_floats() * sizeof(float) + (size_t)kSlWarps * kSlMaxProbesSmem * 4;
+  SOAR_CUDA(cudaFuncSetAttribute(approx_union<Rows>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int a = 1 + ix.spills;
   for (int64_t q0 = 0; q0 < nq; q0 += cq) {
     const int64_t m = std::min(cq, nq - q0);
-    approx_union_fp8<<<ceil_div(m, kSlWarps), 32 * kSlWarps, smem, s>>>(
-        static_cast<const uint8_t*>(ix.vectors), ix.code_stride, ix.row_scales, ix.ids, ix.offsets, ix.assign, a,
-        Qf, qscale, top, tpq, q0, m, t, slice, keys, counts);
+    approx_union<Rows><<<ceil_div(m, kSlWarps), 32 * kSlWarps, smem, s>>>(rws, ix.ids, ix.offsets, ix.assign, a, top,
+                                                                          tpq, q0, m, t, slice, keys, counts);
     SOAR_LAUNCHED();
     select_top_r<<<ceil_div(m, kSlWarps), 32 * kSlWarps, 0, s>>>(keys, counts, m, slice, R, cand + q0 * R);
     SOAR_LAUNCHED();
   }
+}
+
+}  // namespace
+
+void fp8_shortlist(const IndexData& ix, const float* Qf, const float* qscale, const int32_t* top,
+                   const int32_t* tpq, int64_t nq, int t, int R, int32_t* cand, cudaStream_t s, Scratch& scr) {
+  const Fp8Rows rws{static_cast<const uint8_t*>(ix.vectors), ix.code_stride, ix.row_scales, Qf, qscale};
+  run_shortlist(ix, rws, top, tpq, nq, t, R, cand, s, scr);
+}
+
+void pq_shortlist(const IndexData& ix, const float* Qf, int qstride, const int32_t* top, const int32_t* tpq,
+                  int64_t nq, int t, int R, int32_t* cand, cudaStream_t s, Scratch& scr) {
+  const Pq4Rows rws{static_cast<const uint8_t*>(ix.vectors), ix.code_stride, ix.pq_m, ix.d, ix.pq_cb, ix.centroids,
+                    Qf, qstride};
+  run_shortlist(ix, rws, top, tpq, nq, t, R, cand, s, scr);
 }
 
 }  // namespace soar
