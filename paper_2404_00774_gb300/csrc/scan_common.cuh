@@ -83,14 +83,15 @@ int scan_tc_max_k(const IndexData& ix);
 void set_scan_wait_limit(long long cycles);
 int scan_tc_list_len(int k);
 
-// Query-major exact scan (scan_query.cu): a warp per query over its probed
-// partitions (top [nq][t], tpq per-query counts or null) in the core-matrix
-// rows, the exact top k (k <= 32) of every query, spilled copies removed,
-// into ids_out / scores_out.  Usable when the batch probes few pairs per
-// partition (nq * t <= 2c), k <= 32 and the rows have at most 1 024 columns.
+// Query-major exact scan (scan_query.cu): a warp per (query, probe) pair
+// (top [nq][t], tpq per-query counts or null) over the core-matrix rows;
+// lists [nq * t][k] get each pair's exact top k (k <= 32), best first, an id
+// of -1 closing a shorter list, for the caller's k-way merge.  Usable when
+// the batch probes few pairs per partition (nq * t <= 2c), k <= 32 and the
+// rows have at most 1 024 columns.
 bool scan_by_query_usable(const IndexData& ix, int64_t nq, int t, int k);
 void scan_by_query(const IndexData& ix, const float* Qf, int qstride, const int32_t* top, const int32_t* tpq,
-                   int64_t nq, int t, int k, int64_t* ids_out, float* scores_out, cudaStream_t s);
+                   int64_t nq, int t, int k, Cand* lists, cudaStream_t s);
 
 // FP8 shortlist (shortlist.cu): for every query the ids of the R best
 // approximate scores s_q * s_x * sum q8 x8 over its probed union, each point

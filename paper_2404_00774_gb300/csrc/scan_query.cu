@@ -6,15 +6,17 @@
 // item.  When a partition is probed by about one query (many partitions, few
 // queries: two-level selection over 10^5 partitions, or a small serving
 // batch), those items run almost empty and the scan is bound by per-tile
-// epilogue work instead of HBM.  Here a warp takes one query and walks its
-// probed partitions in the index's core-matrix copy of the rows: lane l
-// scores row l of each 32-row block (four 8-row groups, so one 16-byte load
-// per lane covers four whole 128-byte lines), the exact fp32 dot product of
-// the stored row with the query (elements in ascending order, the query in
-// shared memory), and the warp keeps the k best (score, id) rank keys, lane
-// j the j-th, dropping the second copy of a spilled point (its key is
-// bit-identical).  Every probed (query, partition) pair reads its rows once;
-// there is no grouping of pairs, no candidate list and no finishing pass.
+// epilogue work instead of HBM.  Here a warp takes one (query, probe) pair
+// and walks that partition in the index's core-matrix copy of the rows:
+// lane l scores row l of each 32-row block (four 8-row groups, so one
+// 16-byte load per lane covers four whole 128-byte lines), the exact fp32
+// dot product of the stored row with the query (elements in ascending order,
+// the query in shared memory), and the warp keeps the pair's k best (score,
+// id) rank keys, lane j the j-th.  Each pair's list is written best first;
+// the caller's k-way merge over a query's lists drops the second copy of a
+// spilled point (its exact score and id are identical).  Every probed pair
+// reads its rows once; a warp per pair keeps the whole GPU busy even for a
+// batch of a few queries.
 #include "internal.cuh"
 #include "scan_common.cuh"
 
@@ -60,61 +62,63 @@ template <typename T>
 __global__ void __launch_bounds__(32 * kQmWarps) scan_by_query_kernel(
     const T* __restrict__ rows, int kp, const int32_t* __restrict__ row_ids, const int64_t* __restrict__ gstart,
     const float* __restrict__ Qf, int qstride, const int32_t* __restrict__ top, const int32_t* __restrict__ tpq,
-    int64_t nq, int t, int k, int64_t* __restrict__ ids_out, float* __restrict__ scores_out) {
+    int64_t nq, int t, int k, Cand* __restrict__ lists) {
   constexpr unsigned kFull = 0xffffffffu;
   constexpr int E = Chunk<T>::E;
   extern __shared__ __align__(16) float q_all[];   // [kQmWarps][kp]
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t q = (int64_t)blockIdx.x * kQmWarps + w;
-  if (q >= nq) return;                              // uniform within the warp
+  const int64_t e = (int64_t)blockIdx.x * kQmWarps + w;   // pair q * t + j
+  if (e >= nq * t) return;                                // uniform within the warp
+  const int64_t q = e / t;
+  const int j = (int)(e - q * t);
+  Cand* out = lists + e * k;
+  const int tq = tpq ? min(max(tpq[q], 0), t) : t;
+  if (j >= tq) {                                          // probe not taken: an empty list
+    if (lane < k) out[lane] = Cand{-INFINITY, -1};
+    return;
+  }
   float* qs = q_all + w * kp;
   for (int i = lane; i < kp; i += 32) qs[i] = Qf[q * (int64_t)qstride + i];
   __syncwarp();
-  const int tq = tpq ? min(max(tpq[q], 0), t) : t;
   uint64_t mine = ~0ull;          // lane j < k: the j-th best key so far (empty: after every real key)
   uint64_t thr = ~0ull;           // the k-th best key
-  auto insert_round = [&](uint64_t key) {
+  const int chunks = kp / E;
+  const size_t group_bytes = (size_t)8 * kp * sizeof(T);
+  const unsigned char* base = reinterpret_cast<const unsigned char*>(rows) + (lane & 7) * 16;
+  const int p = top[e];
+  const int64_t g1 = gstart[p + 1];
+  for (int64_t g = gstart[p]; g < g1; g += 4) {
+    const int64_t gl = g + (lane >> 3);
+    uint64_t key = ~0ull;
+    if (gl < g1) {
+      const int32_t id = row_ids[gl * 8 + (lane & 7)];
+      if (id >= 0) {                                // -1: padding row of the group
+        const unsigned char* x = base + gl * group_bytes;
+        float acc = 0.f;
+#pragma unroll 8
+        for (int c = 0; c < chunks; ++c)
+          acc = Chunk<T>::dot(__ldg(reinterpret_cast<const uint4*>(x + c * 128)), qs + c * E, acc);
+        key = rank_key(acc, (uint32_t)id);
+      }
+    }
+    // the 32 keys of this block into the warp's top k, one at a time
     unsigned bal = __ballot_sync(kFull, key < thr);
     while (bal) {
       const int src = __ffs(bal) - 1;
       bal &= bal - 1;
       const uint64_t kk = __shfl_sync(kFull, key, src);
       if (kk >= thr) continue;                                   // the same in every lane
-      if (__ballot_sync(kFull, lane < k && mine == kk)) continue;  // spilled copy already in
       const int pos = __popc(__ballot_sync(kFull, lane < k && mine < kk));
       const uint64_t up = __shfl_up_sync(kFull, mine, 1);
       if (lane > pos && lane < k) mine = up;
       if (lane == pos) mine = kk;
       thr = __shfl_sync(kFull, mine, k - 1);
     }
-  };
-  const int chunks = kp / E;
-  const size_t group_bytes = (size_t)8 * kp * sizeof(T);
-  const unsigned char* base = reinterpret_cast<const unsigned char*>(rows) + (lane & 7) * 16;
-  for (int j = 0; j < tq; ++j) {
-    const int p = top[q * t + j];
-    const int64_t g1 = gstart[p + 1];
-    for (int64_t g = gstart[p]; g < g1; g += 4) {
-      const int64_t gl = g + (lane >> 3);
-      uint64_t key = ~0ull;
-      if (gl < g1) {
-        const int32_t id = row_ids[gl * 8 + (lane & 7)];
-        if (id >= 0) {                                // -1: padding row of the group
-          const unsigned char* x = base + gl * group_bytes;
-          float acc = 0.f;
-#pragma unroll 8
-          for (int c = 0; c < chunks; ++c)
-            acc = Chunk<T>::dot(__ldg(reinterpret_cast<const uint4*>(x + c * 128)), qs + c * E, acc);
-          key = rank_key(acc, (uint32_t)id);
-        }
-      }
-      insert_round(key);
-    }
   }
   if (lane < k) {
     const bool have = mine != ~0ull;
-    ids_out[q * k + lane] = have ? (int64_t)(uint32_t)(mine & 0xffffffffu) : -1;
-    scores_out[q * k + lane] = have ? key_float(~(uint32_t)(mine >> 32)) : -INFINITY;
+    out[lane] = have ? Cand{key_float(~(uint32_t)(mine >> 32)), (int32_t)(uint32_t)(mine & 0xffffffffu)}
+                     : Cand{-INFINITY, -1};
   }
 }
 
@@ -127,17 +131,17 @@ bool scan_by_query_usable(const IndexData& ix, int64_t nq, int t, int k) {
 }
 
 void scan_by_query(const IndexData& ix, const float* Qf, int qstride, const int32_t* top, const int32_t* tpq,
-                   int64_t nq, int t, int k, int64_t* ids_out, float* scores_out, cudaStream_t s) {
+                   int64_t nq, int t, int k, Cand* lists, cudaStream_t s) {
   const size_t smem = (size_t)kQmWarps * ix.tc_kp * sizeof(float);
-  const unsigned grid = ceil_div(nq, kQmWarps);
+  const unsigned grid = ceil_div(nq * t, kQmWarps);
   if (ix.dtype == SOAR_F32)
     scan_by_query_kernel<float><<<grid, 32 * kQmWarps, smem, s>>>(
         static_cast<const float*>(ix.tc_rows), ix.tc_kp, ix.tc_ids, ix.tc_gstart, Qf, qstride, top, tpq, nq, t, k,
-        ids_out, scores_out);
+        lists);
   else
     scan_by_query_kernel<__nv_bfloat16><<<grid, 32 * kQmWarps, smem, s>>>(
         static_cast<const __nv_bfloat16*>(ix.tc_rows), ix.tc_kp, ix.tc_ids, ix.tc_gstart, Qf, qstride, top, tpq,
-        nq, t, k, ids_out, scores_out);
+        nq, t, k, lists);
   SOAR_LAUNCHED();
 }
 

@@ -1045,9 +1045,18 @@ void search(const IndexData& ix, const void* Q, soar_dtype dt, int64_t nq, int32
     }
     stage_mark(s, "select", false);
     if (scan_by_query_usable(ix, nq, t, k)) {   // few queries per probed partition: query-major exact scan
+      Cand* lists = scr.get<Cand>((size_t)nq * t * k);
       stage_mark(s, "scan", true);
-      scan_by_query(ix, Qf, qstride, top, tpq, nq, t, k, ids_out, scores_out, s);
+      scan_by_query(ix, Qf, qstride, top, tpq, nq, t, k, lists, s);
       stage_mark(s, "scan", false);
+      // k-way merge of each query's t lists; a spilled copy repeats (score, id) and is dropped
+      const int smem = 4 * t * (int)sizeof(uint16_t);
+      SOAR_CUDA(cudaFuncSetAttribute(merge_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+      stage_mark(s, "merge", true);
+      merge_kernel<false><<<ceil_div(nq, 4), 128, smem, s>>>(lists, k, nq, 0, nullptr, nullptr, t, k, ids_out,
+                                                             nullptr, scores_out);
+      SOAR_LAUNCHED();
+      stage_mark(s, "merge", false);
       return;
     }
     const int64_t P = nq * t;
