@@ -70,6 +70,8 @@ def parse_args():
                         "partitions) workloads at full size")
     p.add_argument("--leg", choices=["precision", "serving", "multilevel", "layouts"], default=None,
                    help="run one full-size workload alone and print its results")
+    p.add_argument("--scale", type=float, default=1.0,
+                   help="with --leg multilevel: shrink n and the partition counts by this factor")
     p.add_argument("--arms", choices=["all", "main"], default="all",
                    help="all: SOAR at lambda 0.5/1/2, spill without SOAR, no spill; main: the timed arm only")
     return p.parse_args()
@@ -765,7 +767,7 @@ def precision_at_size(sb, dev, steps, warmup, n_train=1_000_000, n_test=10_000, 
 # ------------------------------------------------------------------ GPU arm
 
 def multilevel_at_size(sb, dev, steps, warmup, c2=1000, train_rows=1_000_000, coarse_iters=10,
-                       t1s=(4, 8, 16, 32, 64, 128)):
+                       t1s=(4, 8, 16, 32, 64, 128), scale=1.0):
     """Two-level partition selection (App. A.4, general index setup; Section
     4) where flat selection costs: 10^7 unit vectors (d = 96, bf16, a
     10 000-component isotropic mixture drawn on the device) in c = 10^5
@@ -775,9 +777,15 @@ def multilevel_at_size(sb, dev, steps, warmup, c2=1000, train_rows=1_000_000, co
     Flat selection (S = Q C^T over all 10^5 centroids, top t) is run at the
     smallest t reaching recall@10 >= 0.9; the two-level selection probes t1
     coarse partitions and keeps the same t.  Per t1: recall, selection ms
-    (the selection call alone), whole-search ms and QPS."""
+    (the selection call alone), whole-search ms and QPS.  ``scale`` < 1
+    shrinks n, c, c2 and the training rows together (a smaller case of the
+    same shape, for profiling)."""
+    import dataclasses
     import torch
     w = synth.WORKLOADS["multilevel"]
+    if scale != 1.0:
+        w = dataclasses.replace(w, n=int(w.n * scale), c=int(w.c * scale))
+        c2, train_rows = max(16, int(c2 * scale)), int(train_rows * scale)
     mix = synth.mixture_for(w)
     X = synth.sample_on_device(mix, w.n, w.data_seed, dev, torch.bfloat16)
     Q = synth.sample_on_device(mix, w.nq, w.query_seed, dev, torch.float32)
@@ -1118,7 +1126,7 @@ def run_leg(args):
     dev = torch.device("cuda", 0)
     legs = {"precision": lambda: precision_at_size(sb, dev, args.steps, args.warmup),
             "serving": lambda: serving_at_size(sb, dev),
-            "multilevel": lambda: multilevel_at_size(sb, dev, args.steps, args.warmup),
+            "multilevel": lambda: multilevel_at_size(sb, dev, args.steps, args.warmup, scale=args.scale),
             "layouts": lambda: glove_layouts(sb, dev, args.steps, args.warmup)}
     print(json.dumps({args.leg: legs[args.leg]()}), flush=True)
     return 0

@@ -7,7 +7,8 @@
 // by cp.async.bulk straight from the index, which stores every partition in
 // that same layout.  Per tile one thread issues one tcgen05.mma per 32 bytes
 // of K (kind::tf32 for an fp32 index, kind::f16 with bf16 operands for a
-// bf16 index) into one of two TMEM accumulators (128 lanes x 64 columns);
+// bf16 index) into one of four TMEM accumulators (128 lanes x 64 columns,
+// so the MMAs run up to three tiles ahead of the epilogue);
 // four epilogue warps read the scores back (lane = query).
 //
 // Screening.  kind::tf32 truncates each fp32 operand to 10 mantissa bits,
@@ -54,6 +55,7 @@ constexpr int kM = 128;        // query slots per item (MMA M)
 constexpr int kN = 64;         // rows per tile (MMA N)
 constexpr int kThreads = 224;  // producer, MMA issuer, gate, 4 epilogue warps
 constexpr int kMaxStages = 4;
+constexpr int kNB = 4;         // TMEM accumulator buffers (kN columns each)
 constexpr int kCand = 32;      // candidate rows kept per (query, partition), register mode
 constexpr int kWideK = kTcWideK;   // largest k of the heap mode
 constexpr int kWideList = kTcWideList;   // largest global candidate list of the heap mode
@@ -143,7 +145,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
   // lanes of a warp always touch 32 distinct banks
   float* ext_s = av_s + kN * kM;   // candidates [kCand][kM] (+ rows) or the heap [k][kM]
   uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(ext_s) + ext_bytes(k));
-  // bars: full[S], empty[S], tfull[2], tempty[2]
+  // bars: full[S], empty[S], tfull[kNB], tempty[kNB]
   __shared__ uint32_t tmem_base_s;
   __shared__ ItemDesc item_s;
   __shared__ int abort_s;
@@ -153,14 +155,14 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
   auto full = [&](int s) { return tc::smem_u32(&bars[s]); };
   auto empty = [&](int s) { return tc::smem_u32(&bars[S + s]); };
   auto tfull = [&](int b) { return tc::smem_u32(&bars[2 * S + b]); };
-  auto tempty = [&](int b) { return tc::smem_u32(&bars[2 * S + 2 + b]); };
+  auto tempty = [&](int b) { return tc::smem_u32(&bars[2 * S + kNB + b]); };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       tc::bar_init(full(s), 1);
       tc::bar_init(empty(s), 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kNB; ++b) {
       tc::bar_init(tfull(b), 1);
       tc::bar_init(tempty(b), 4);
     }
@@ -168,7 +170,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
     abort_s = 0;
     issued_s = consumed_s = committed_s = 0;
   }
-  if (warp == 1) tc::tmem_alloc(tc::smem_u32(&tmem_base_s), 2 * kN);
+  if (warp == 1) tc::tmem_alloc(tc::smem_u32(&tmem_base_s), kNB * kN);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -290,7 +292,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
       // barrier that also carries the stop flag.
       for (int i = 0; i < ntiles; ++i) {
         if (tc::named_bar_or(2, 64, false)) break;
-        const uint32_t T = tile_ctr + i, s = T % S, b = T & 1;
+        const uint32_t T = tile_ctr + i, s = T % S, b = T % kNB;
         if (lane == 0) {
           tc::fence_after_sync();
           const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB) + s * b_bytes;
@@ -315,7 +317,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
       // ---- gate: waits for each tile's stage and TMEM buffer, then releases
       // the MMA issuer
       for (int i = 0; i < ntiles; ++i) {
-        const uint32_t T = tile_ctr + i, s = T % S, ph = (T / S) & 1, b = T & 1, tph = (T >> 1) & 1;
+        const uint32_t T = tile_ctr + i, s = T % S, ph = (T / S) & 1, b = T % kNB, tph = (T / kNB) & 1;
         int ok = 1;
         if (lane == 0) {
           ok = tc::bar_wait(full(s), ph, abort_v, P.wait_limit) &&
@@ -355,7 +357,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
       int hn = 0;
       Cand* glist = P.cand + (e0 + (active ? jq : 0)) * (int64_t)P.kc;     // heap mode candidates
       for (int i = 0; i < ntiles; ++i) {
-        const uint32_t T = tile_ctr + i, b = T & 1, tph = (T >> 1) & 1;
+        const uint32_t T = tile_ctr + i, b = T % kNB, tph = (T / kNB) & 1;
         const bool ok = tc::bar_wait(tfull(b), tph, abort_v, P.wait_limit);
         if (!ok) give_up();
         tc::fence_after_sync();
@@ -544,18 +546,18 @@ __global__ void __launch_bounds__(kThreads, 1) scan_tc_kernel(TcParams P) {
   if (abort_s && threadIdx.x == 64 && committed_s > 0) {
     volatile int never = 0;
     const int T = committed_s - 1;
-    tc::bar_wait(tfull(T & 1), (T >> 1) & 1, &never);
+    tc::bar_wait(tfull(T % kNB), (T / kNB) & 1, &never);
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  if (warp == 1) tc::tmem_dealloc(tmem, 2 * kN);
+  if (warp == 1) tc::tmem_dealloc(tmem, kNB * kN);
 }
 
 size_t smem_bytes(int kp, int k, int stages, int es) {
   // the A operand takes kM * kp * 4 bytes either way (fp32, or bf16 hi and lo)
   return 1024 + (size_t)kM * kp * 4 + (size_t)stages * kN * kp * es + (size_t)kN * kM * 4 + ext_bytes(k) +
-         (size_t)(2 * stages + 4) * 8;
+         (size_t)(2 * stages + 2 * kNB) * 8;
 }
 
 // delta / (||q|| max_p ||x||) of the screen (see the header comment)

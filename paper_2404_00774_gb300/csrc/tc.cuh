@@ -70,13 +70,15 @@ __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, volatile
   return true;
 }
 
-// bar_wait for roles that may wait long (producer, MMA issuer, epilogue):
-// each poll suspends the thread for up to a microsecond.
-__device__ __forceinline__ bool bar_wait_sleep(uint32_t bar, uint32_t parity, volatile int* abort) {
+// bar_wait for roles that may wait long (producer, gate, epilogue): each
+// poll suspends the thread for up to `ns` nanoseconds instead of spinning on
+// the issue slots of the warps sharing its scheduler.
+__device__ __forceinline__ bool bar_wait_sleep(uint32_t bar, uint32_t parity, volatile int* abort,
+                                               long long limit = kWaitLimit, uint32_t ns = 1000u) {
   const long long t0 = clock64();
-  while (!bar_try_wait_sleep(bar, parity, 1000u)) {
+  while (!bar_try_wait_sleep(bar, parity, ns)) {
     if (*abort) return false;
-    if (clock64() - t0 > (1ll << 31)) return false;
+    if (clock64() - t0 > limit) return false;
   }
   return true;
 }
