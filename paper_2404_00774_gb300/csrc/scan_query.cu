@@ -11,8 +11,10 @@
 // lane l scores row l of each 32-row block (four 8-row groups, so one
 // 16-byte load per lane covers four whole 128-byte lines), the exact fp32
 // dot product of the stored row with the query (elements in ascending order,
-// the query in shared memory), and the warp keeps the pair's k best (score,
-// id) rank keys, lane j the j-th.  Each pair's list is written best first;
+// the query in shared memory), two rows per lane in flight, and the warp
+// keeps the pair's 32 best (score, id) rank keys, lane j the j-th: a block
+// with many newcomers is sorted across the warp and merged (bitonic), a
+// block with few is inserted key by key.  Each pair's list is written best first;
 // the caller's k-way merge over a query's lists drops the second copy of a
 // spilled point (its exact score and id are identical).  Every probed pair
 // reads its rows once; a warp per pair keeps the whole GPU busy even for a
@@ -58,6 +60,54 @@ template <> struct Chunk<__nv_bfloat16> {
   }
 };
 
+// Ascending sort of one 64-bit key per lane across the warp (bitonic network).
+__device__ __forceinline__ uint64_t warp_sort_keys(uint64_t v, int lane) {
+#pragma unroll
+  for (int kk = 2; kk <= 32; kk <<= 1)
+#pragma unroll
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      const uint64_t o = __shfl_xor_sync(0xffffffffu, v, j);
+      const bool keep_min = ((lane & j) == 0) == ((lane & kk) == 0);
+      v = keep_min ? (o < v ? o : v) : (o > v ? o : v);
+    }
+  return v;
+}
+
+// The warp's running 32 smallest keys (lane j: the j-th, ascending) merged
+// with a block of 32 keys, one per lane.
+__device__ __forceinline__ uint64_t merge_block(uint64_t mine, uint64_t key, uint64_t thr, int lane) {
+  constexpr unsigned kFull = 0xffffffffu;
+  unsigned bal = __ballot_sync(kFull, key < thr);
+  if (__popc(bal) >= 4) {
+    // many newcomers: sort the block, take the lane-wise minimum of the list
+    // and the reversed block (a bitonic sequence holding the 32 smallest of
+    // both), then sort that sequence
+    const uint64_t b = warp_sort_keys(key, lane);
+    const uint64_t r = __shfl_sync(kFull, b, 31 - lane);
+    uint64_t c = r < mine ? r : mine;
+#pragma unroll
+    for (int j = 16; j > 0; j >>= 1) {
+      const uint64_t o = __shfl_xor_sync(kFull, c, j);
+      c = (lane & j) == 0 ? (o < c ? o : c) : (o > c ? o : c);
+    }
+    return c;
+  }
+  // a few newcomers: insert them one at a time
+  uint64_t t31 = thr;
+  while (bal) {
+    const int src = __ffs(bal) - 1;
+    bal &= bal - 1;
+    const uint64_t kk = __shfl_sync(kFull, key, src);
+    if (kk >= t31) continue;
+    const int pos = __popc(__ballot_sync(kFull, mine < kk));
+    const uint64_t up = __shfl_up_sync(kFull, mine, 1);
+    if (lane > pos) mine = up;
+    if (lane == pos) mine = kk;
+    t31 = __shfl_sync(kFull, mine, 31);
+  }
+  return mine;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(32 * kQmWarps) scan_by_query_kernel(
     const T* __restrict__ rows, int kp, const int32_t* __restrict__ row_ids, const int64_t* __restrict__ gstart,
@@ -77,43 +127,38 @@ __global__ void __launch_bounds__(32 * kQmWarps) scan_by_query_kernel(
     if (lane < k) out[lane] = Cand{-INFINITY, -1};
     return;
   }
+  const int p = top[e];
   float* qs = q_all + w * kp;
   for (int i = lane; i < kp; i += 32) qs[i] = Qf[q * (int64_t)qstride + i];
   __syncwarp();
-  uint64_t mine = ~0ull;          // lane j < k: the j-th best key so far (empty: after every real key)
-  uint64_t thr = ~0ull;           // the k-th best key
+  // the 32 best keys so far, lane j the j-th (~0: empty); the list keeps 32
+  // entries whatever k, and its first k are the pair's top k
+  uint64_t mine = ~0ull;
   const int chunks = kp / E;
   const size_t group_bytes = (size_t)8 * kp * sizeof(T);
   const unsigned char* base = reinterpret_cast<const unsigned char*>(rows) + (lane & 7) * 16;
-  const int p = top[e];
   const int64_t g1 = gstart[p + 1];
-  for (int64_t g = gstart[p]; g < g1; g += 4) {
-    const int64_t gl = g + (lane >> 3);
-    uint64_t key = ~0ull;
-    if (gl < g1) {
-      const int32_t id = row_ids[gl * 8 + (lane & 7)];
-      if (id >= 0) {                                // -1: padding row of the group
-        const unsigned char* x = base + gl * group_bytes;
-        float acc = 0.f;
-#pragma unroll 8
-        for (int c = 0; c < chunks; ++c)
-          acc = Chunk<T>::dot(__ldg(reinterpret_cast<const uint4*>(x + c * 128)), qs + c * E, acc);
-        key = rank_key(acc, (uint32_t)id);
-      }
+  // two 32-row blocks per iteration (lane l: row l of each), so that each
+  // lane has two rows' loads in flight
+  for (int64_t g = gstart[p]; g < g1; g += 8) {
+    const int64_t ga = g + (lane >> 3), gb = ga + 4;
+    const bool va = ga < g1, vb = gb < g1;
+    const int32_t ida = va ? row_ids[ga * 8 + (lane & 7)] : -1;
+    const int32_t idb = vb ? row_ids[gb * 8 + (lane & 7)] : -1;
+    const unsigned char* xa = base + (va ? ga : 0) * group_bytes;
+    const unsigned char* xb = base + (vb ? gb : 0) * group_bytes;
+    float acc_a = 0.f, acc_b = 0.f;
+#pragma unroll 2
+    for (int c = 0; c < chunks; ++c) {
+      const uint4 wa = __ldg(reinterpret_cast<const uint4*>(xa + c * 128));
+      const uint4 wb = __ldg(reinterpret_cast<const uint4*>(xb + c * 128));
+      acc_a = Chunk<T>::dot(wa, qs + c * E, acc_a);
+      acc_b = Chunk<T>::dot(wb, qs + c * E, acc_b);
     }
-    // the 32 keys of this block into the warp's top k, one at a time
-    unsigned bal = __ballot_sync(kFull, key < thr);
-    while (bal) {
-      const int src = __ffs(bal) - 1;
-      bal &= bal - 1;
-      const uint64_t kk = __shfl_sync(kFull, key, src);
-      if (kk >= thr) continue;                                   // the same in every lane
-      const int pos = __popc(__ballot_sync(kFull, lane < k && mine < kk));
-      const uint64_t up = __shfl_up_sync(kFull, mine, 1);
-      if (lane > pos && lane < k) mine = up;
-      if (lane == pos) mine = kk;
-      thr = __shfl_sync(kFull, mine, k - 1);
-    }
+    const uint64_t ka = ida >= 0 ? rank_key(acc_a, (uint32_t)ida) : ~0ull;   // -1: padding row or past the end
+    const uint64_t kb = idb >= 0 ? rank_key(acc_b, (uint32_t)idb) : ~0ull;
+    mine = merge_block(mine, ka, __shfl_sync(kFull, mine, 31), lane);
+    mine = merge_block(mine, kb, __shfl_sync(kFull, mine, 31), lane);
   }
   if (lane < k) {
     const bool have = mine != ~0ull;
