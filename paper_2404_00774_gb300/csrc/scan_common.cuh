@@ -78,6 +78,15 @@ bool scan_tc_search(const IndexData& ix, const IvfWork& work, int max_items, con
                     const int32_t* top, const int32_t* inv, const int32_t* tpq, int64_t nq, int t, int k,
                     Cand* lists, int* err, int64_t* ids_out, float* scores_out, cudaStream_t s, Scratch& scr);
 int scan_tc_max_k(const IndexData& ix);
+// Candidate-list length per pair slot of the group-maxima scan (scan_gm.cu),
+// which takes k <= 16 when its shared memory fits the row width.
+constexpr int kGmList = 64;
+bool scan_gm_usable(const IndexData& ix, int k);
+// Launches it (after the caller cleared the headers, set the bounds to -inf
+// and zeroed the work counter); lists [pairs][kGmList].
+void scan_gm_launch(const IndexData& ix, const IvfWork& work, int grid, const float* Qf, const float* qnorm,
+                    int64_t nq, int k, float dscale, long long wait_limit, int* counter, int* err,
+                    unsigned* gbound, Cand* lists, int2* hdr, cudaStream_t s, Scratch& scr);
 // SM cycles a pipeline wait of the scan may take before its CTA gives up
 // (0: the default of about a second); the teardown's waits keep the default.
 void set_scan_wait_limit(long long cycles);

@@ -60,10 +60,14 @@ constexpr int kCand = 32;      // candidate rows kept per (query, partition), re
 constexpr int kWideK = kTcWideK;   // largest k of the heap mode
 constexpr int kWideList = kTcWideList;   // largest global candidate list of the heap mode
 
-// Candidate-list length per (query, partition) slot: kCand for k <= 32, else
-// 2k rounded up to a warp multiple (room to append between compactions).
+// Candidate-list length per (query, partition) slot: kGmList for k <= 16
+// (the group-maxima scan of scan_gm.cu appends without a final filter),
+// kCand for k <= 32, else 2k rounded up to a warp multiple (room to append
+// between compactions).
 __host__ __device__ constexpr int list_len_for(int k) {
-  return k <= kCand ? kCand : ((2 * k + 31) / 32 * 32 > kWideList ? kWideList : (2 * k + 31) / 32 * 32);
+  return k <= 16 ? kGmList
+                 : k <= kCand ? kCand
+                              : ((2 * k + 31) / 32 * 32 > kWideList ? kWideList : (2 * k + 31) / 32 * 32);
 }
 
 // Shared memory behind the tile scores: register mode keeps kCand candidates
@@ -633,8 +637,13 @@ bool scan_tc_search(const IndexData& ix, const IvfWork& work, int max_items, con
   const size_t smem = smem_bytes(ix.tc_kp, k, stages, es);
   const int grid = std::max(1, std::min(max_items, num_sms()));
   stage_mark(s, "scan", true);
-  if (es == 4) launch_scan_tc<float>(k, grid, smem, s, prm);
-  else launch_scan_tc<__nv_bfloat16>(k, grid, smem, s, prm);
+  if (scan_gm_usable(ix, k))
+    scan_gm_launch(ix, work, grid, Qf, qnorm, nq, k, prm.dscale, prm.wait_limit, prm.counter, err, prm.gbound,
+                   lists, hdr, s, scr);
+  else if (es == 4)
+    launch_scan_tc<float>(k, grid, smem, s, prm);
+  else
+    launch_scan_tc<__nv_bfloat16>(k, grid, smem, s, prm);
   stage_mark(s, "scan", false);
   stage_mark(s, "rescore", true);
   if (k <= kCand) {

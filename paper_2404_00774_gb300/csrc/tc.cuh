@@ -200,6 +200,15 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
       : "r"(taddr)
       : "memory");
 }
+// Four columns of this warp's 32 TMEM lanes (one lane per thread) and their
+// maximum, computed by the load itself (tcgen05.ld.red, sm_103a).
+__device__ __forceinline__ void tmem_ld4_max(uint32_t taddr, uint32_t* r, float& mx) {
+  asm volatile("tcgen05.ld.red.sync.aligned.32x32b.x4.max.f32 {%0, %1, %2, %3}, %4, [%5];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=f"(mx)
+               : "r"(taddr)
+               : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 }  // namespace tc

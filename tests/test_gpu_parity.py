@@ -323,6 +323,35 @@ def test_search_pads_when_candidates_run_out(soar):
     ix.close()
 
 
+@pytest.mark.parametrize("k,t", [(5, 1), (10, 1), (16, 1), (16, 2)])
+def test_search_short_partitions_few_probes(soar, k, t):
+    # Partitions of about 60 rows (one short tile each), probed by one or two
+    # partitions per query: a query's first partition starts without a bound
+    # from the others, and at k = 16 a tile of fewer than 61 rows has fewer
+    # than k groups of four, so the screening cut stays at -inf for the whole
+    # partition.  Rows past a partition's end (the tile's padding) must still
+    # never become candidates: they would be rescored as rows of the next
+    # partition.
+    mix = synth.Mixture(24, 12, "isotropic", 0.3, param_seed=41)
+    X = mix.sample(1500, seed=42)
+    Q = mix.sample(400, seed=43)
+    C = oracle.kmeans(X, synth.init_indices(1500, 50, seed=44), 3)
+    A = oracle.soar_assign(X, C, 1.0, 1)
+    off, ids = oracle.build_ivf(A, 50)
+    assert np.median(np.diff(off)) < 64
+    ix = soar.soar_index_build(_t(X), _t(C), _t(A))
+    try:
+        gi, gs = soar.soar_search(ix, _t(Q), k, t)
+        wi, ws = oracle.ivf_search(Q, X, C, off, ids, k, t)
+        gi, gs = gi.cpu().numpy(), gs.cpu().numpy()
+        np.testing.assert_array_equal(gi < 0, wi < 0)
+        assert topk_mismatches(gi, wi, ws, _exact(X, Q)) == []
+        mx, mean = score_errors(gi, gs, _exact(X, Q))
+        assert mx < 1e-5, (mx, mean)
+    finally:
+        ix.close()
+
+
 def test_search_equal_rows_overflow_candidate_lists(soar):
     # 48 identical rows in one partition tie exactly for queries sitting on
     # them: more candidates than a screened list holds, so the exact rescan of
