@@ -6,15 +6,17 @@
 // codes of every copy's residual x - C_p (approximate score <q, C_p> +
 // sum_s <q_s, B[s][code_s]>).
 //
-// Two kernels, a warp per query:
-//   approx_union  walks the query's probed partitions (lane = row, code rows
-//                 read coalesced), drops a copy when the point has another
-//                 copy in a partition the query probed earlier (from the
-//                 index's copy of the assignment: each point counts once),
-//                 and writes one 64-bit rank key per remaining point
-//                 (approximate score descending, then id ascending) into the
-//                 query's slice of a key buffer;
-//   select_top_r  finds the R smallest keys of the slice by an MSB-first
+// Three kernels:
+//   pair_offsets  each probed pair's place in its query's slice of a key
+//                 buffer (the sizes of the earlier probed partitions);
+//   approx_pairs  a warp per (query, probe) pair scores the partition's rows
+//                 (lane = row, code rows read coalesced), drops a copy when
+//                 the point has another copy in a partition the query probed
+//                 earlier (from the index's copy of the assignment: each
+//                 point counts once) and writes one 64-bit rank key per row
+//                 (approximate score descending, then id ascending; the
+//                 all-ones key for a dropped copy);
+//   select_top_r  a warp per query finds the R smallest keys of its slice by an MSB-first
 //                 radix select over bytes (warp histograms in shared memory;
 //                 the keys are distinct, so the selected set is exact) and
 //                 writes their ids.
@@ -109,57 +111,70 @@ struct Pq4Rows {
   }
 };
 
+// Each probed pair's first position in its query's key slice: the sizes of
+// the query's earlier probed partitions added up (a thread per query).
+__global__ void pair_offsets(const int64_t* __restrict__ off, const int32_t* __restrict__ top,
+                             const int32_t* __restrict__ tpq, int64_t q0, int64_t nq, int t,
+                             int64_t* __restrict__ pos, int64_t* __restrict__ counts) {
+  const int64_t ql = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (ql >= nq) return;
+  const int64_t q = q0 + ql;
+  const int tq = tpq ? min(max(tpq[q], 0), t) : t;
+  int64_t acc = 0;
+  for (int j = 0; j < tq; ++j) {
+    pos[ql * t + j] = acc;
+    const int p = top[q * (int64_t)t + j];
+    acc += off[p + 1] - off[p];
+  }
+  counts[ql] = acc;
+}
+
+// A warp per (query, probe) pair: the approximate score of every row of the
+// probed partition, written as a rank key at the pair's place in the query's
+// slice; a copy whose point has another copy in a partition the query probed
+// earlier writes the all-ones key instead (it sorts after every real key and
+// its id bits read as -1).
 template <typename Rows>
-__global__ void __launch_bounds__(32 * kSlWarps) approx_union(
+__global__ void __launch_bounds__(32 * kSlWarps) approx_pairs(
     Rows rows, const int32_t* __restrict__ ids, const int64_t* __restrict__ off, const int32_t* __restrict__ assign,
     int a, const int32_t* __restrict__ top, const int32_t* __restrict__ tpq, int64_t q0, int64_t nq, int t,
-    int64_t slice, uint64_t* __restrict__ keys, int64_t* __restrict__ counts) {
-  constexpr unsigned kFull = 0xffffffffu;
+    int64_t slice, const int64_t* __restrict__ pos, uint64_t* __restrict__ keys) {
   extern __shared__ __align__(16) unsigned char sl_smem[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t ql = (int64_t)blockIdx.x * kSlWarps + w;   // query within this chunk
-  if (ql >= nq) return;                                   // uniform within the warp
+  const int64_t el = (int64_t)blockIdx.x * kSlWarps + w;   // pair within this chunk: ql * t + j
+  if (el >= nq * t) return;                               // uniform within the warp
+  const int64_t ql = el / t;
+  const int j = (int)(el - ql * t);
   const int64_t q = q0 + ql;
+  const int tq = tpq ? min(max(tpq[q], 0), t) : t;
+  if (j >= tq) return;
   const int per = rows.smem_floats();
   float* qs = reinterpret_cast<float*>(sl_smem) + w * per;
   int32_t* probes_s = reinterpret_cast<int32_t*>(reinterpret_cast<float*>(sl_smem) + kSlWarps * per) +
                       w * kSlMaxProbesSmem;
   rows.load(qs, q, lane);
-  const int tq = tpq ? min(max(tpq[q], 0), t) : t;
   const int32_t* probes = top + q * (int64_t)t;
-  if (t <= kSlMaxProbesSmem) {
-    for (int j = lane; j < tq; j += 32) probes_s[j] = probes[j];
+  if (j <= kSlMaxProbesSmem) {
+    for (int jj = lane; jj < j; jj += 32) probes_s[jj] = probes[jj];
     probes = probes_s;
   }
   __syncwarp();
-  uint64_t* out = keys + ql * slice;
-  int64_t n = 0;
-  for (int j = 0; j < tq; ++j) {
-    const int p = probes[j];
-    const float base = rows.partition_base(qs, p, lane);
-    const int64_t r0 = off[p], r1 = off[p + 1];
-    for (int64_t rb = r0; rb < r1; rb += 32) {
-      const int64_t r = rb + lane;
-      bool keep = false;
-      uint64_t key = 0;
-      if (r < r1) {
-        const int32_t id = ids[r];
-        keep = true;
-        // the point's copy in an earlier-probed partition is the one that counts
-        for (int i = 0; i < a && keep; ++i) {
-          const int other = assign[(int64_t)id * a + i];
-          if (other == p) continue;
-          for (int jj = 0; jj < j; ++jj)
-            if (probes[jj] == other) { keep = false; break; }
-        }
-        if (keep) key = rank_key(rows.score(qs, q, r, base), (uint32_t)id);
-      }
-      const unsigned bal = __ballot_sync(kFull, keep);
-      if (keep) out[n + __popc(bal & ((1u << lane) - 1u))] = key;
-      n += __popc(bal);
+  const int p = top[q * (int64_t)t + j];
+  const float base = rows.partition_base(qs, p, lane);
+  const int64_t r0 = off[p], r1 = off[p + 1];
+  uint64_t* out = keys + ql * slice + pos[el] - r0;
+  for (int64_t r = r0 + lane; r < r1; r += 32) {
+    const int32_t id = ids[r];
+    bool keep = true;
+    // the point's copy in an earlier-probed partition is the one that counts
+    for (int i = 0; i < a && keep; ++i) {
+      const int other = assign[(int64_t)id * a + i];
+      if (other == p) continue;
+      for (int jj = 0; jj < j; ++jj)
+        if (probes[jj] == other) { keep = false; break; }
     }
+    out[r] = keep ? rank_key(rows.score(qs, q, r, base), (uint32_t)id) : ~0ull;
   }
-  if (lane == 0) counts[ql] = n;
 }
 
 // The R smallest keys of each query's slice -> their ids (cand [nq][R],
@@ -224,14 +239,21 @@ __global__ void __launch_bounds__(32 * kSlWarps) select_top_r(const uint64_t* __
       __syncwarp();
     }
   }
+  // every key below the limit, then keys equal to it (at most one real key:
+  // the keys are distinct) until R are taken; a dropped copy's all-ones key
+  // is never a real candidate, so the rest is padding
   int64_t m = 0;
-  for (int64_t i0 = 0; i0 < n; i0 += 32) {
-    const int64_t i = i0 + lane;
-    const bool take = i < n && K[i] <= limit;
-    const unsigned bal = __ballot_sync(kFull, take);
-    const int64_t pos = m + __popc(bal & ((1u << lane) - 1u));
-    if (take && pos < R) out[pos] = (int32_t)(K[i] & 0xffffffffu);
-    m += __popc(bal);
+  for (int pass = 0; pass < 2 && m < R; ++pass) {
+    if (pass == 1 && limit == ~0ull) break;
+    for (int64_t i0 = 0; i0 < n && m < R; i0 += 32) {
+      const int64_t i = i0 + lane;
+      const uint64_t kk = i < n ? K[i] : ~0ull;
+      const bool take = i < n && (pass == 0 ? kk < limit : kk == limit);
+      const unsigned bal = __ballot_sync(kFull, take);
+      const int64_t pos = m + __popc(bal & ((1u << lane) - 1u));
+      if (take && pos < R) out[pos] = (int32_t)(kk & 0xffffffffu);
+      m += __popc(bal);
+    }
   }
   for (int64_t i = min(m, (int64_t)R) + lane; i < R; i += 32) out[i] = -1;
 }
@@ -246,13 +268,16 @@ void run_shortlist(const IndexData& ix, const Rows& rws, const int32_t* top, con
   const int64_t cq = std::min(chunk, nq);
   uint64_t* keys = scr.get<uint64_t>((size_t)cq * slice);
   int64_t* counts = scr.get<int64_t>(cq);
+  int64_t* pos = scr.get<int64_t>((size_t)cq * t);
   const size_t smem = (size_t)kSlWarps * rws.smem_floats() * sizeof(float) + (size_t)kSlWarps * kSlMaxProbesSmem * 4;
-  SOAR_CUDA(cudaFuncSetAttribute(approx_union<Rows>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  SOAR_CUDA(cudaFuncSetAttribute(approx_pairs<Rows>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int a = 1 + ix.spills;
   for (int64_t q0 = 0; q0 < nq; q0 += cq) {
     const int64_t m = std::min(cq, nq - q0);
-    approx_union<Rows><<<ceil_div(m, kSlWarps), 32 * kSlWarps, smem, s>>>(rws, ix.ids, ix.offsets, ix.assign, a, top,
-                                                                          tpq, q0, m, t, slice, keys, counts);
+    pair_offsets<<<ceil_div(m, 128), 128, 0, s>>>(ix.offsets, top, tpq, q0, m, t, pos, counts);
+    SOAR_LAUNCHED();
+    approx_pairs<Rows><<<ceil_div(m * t, kSlWarps), 32 * kSlWarps, smem, s>>>(rws, ix.ids, ix.offsets, ix.assign, a,
+                                                                              top, tpq, q0, m, t, slice, pos, keys);
     SOAR_LAUNCHED();
     select_top_r<<<ceil_div(m, kSlWarps), 32 * kSlWarps, 0, s>>>(keys, counts, m, slice, R, cand + q0 * R);
     SOAR_LAUNCHED();
