@@ -218,9 +218,12 @@ def max_over_ranks(value, dist=None, device=None):
     return float(t.item())
 
 
+SCAN_KERNEL = "scan_gm_kernel"        # the partition scan for k <= 16 (csrc/scan_gm.cu)
+
+
 def kernel_hash():
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_2404_00774_gb300", "csrc", "scan_tc.cu"), "rb") as f:
+    with open(os.path.join(ROOT, "paper_2404_00774_gb300", "csrc", "scan_gm.cu"), "rb") as f:
         h.update(f.read())
     return h.hexdigest()[:16]
 
@@ -228,7 +231,7 @@ def kernel_hash():
 def profiled_traffic(workload):
     """Per-launch DRAM bytes of the scan kernel from a committed ncu summary,
     if that summary was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", f"scan_tc_kernel_{workload}.txt")
+    path = os.path.join(ROOT, "profiles", f"{SCAN_KERNEL}_{workload}.txt")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
@@ -247,7 +250,8 @@ def scan_roofline(w, nq, k, t, ix, Qd, sb, scan_ms, hbm, bf16, peak_src):
     per row, plus the queries (4d bytes each) and the results (12 bytes per
     neighbour).  The bytes the kernel's own schedule adds (a partition
     re-read for each further chunk of 128 of its queries, the per-pair
-    candidate lists) are reported beside them, not counted."""
+    candidate lists, at most 64 entries of 8 bytes each) are reported beside
+    them, not counted."""
     import torch
     offsets = ix.offsets()
     sizes = offsets[1:] - offsets[:-1]
@@ -263,11 +267,11 @@ def scan_roofline(w, nq, k, t, ix, Qd, sb, scan_ms, hbm, bf16, peak_src):
     flops = 2.0 * w.d * pairs
     gbs = bytes_alg / (scan_ms / 1e3) / 1e9
     return {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-            "peak_source": f"{peak_src} hbm_gbs (copy burst)", "kernel": "scan_tc_kernel",
+            "peak_source": f"{peak_src} hbm_gbs (copy burst)", "kernel": SCAN_KERNEL,
             "ms_per_launch": scan_ms, "algorithmic_bytes": bytes_alg,
             "algorithmic_rule": "distinct probed partitions x rows x (4d + 4) + queries + results",
             "schedule_bytes": {"rows_rereads": (rows_sched - rows_once) * kp * 4,
-                               "candidate_lists": nq * t * 8 * 32, "row_bytes_padded_k": kp * 4},
+                               "candidate_list_capacity": nq * t * 8 * 64, "row_bytes_padded_k": kp * 4},
             "algorithmic_flops": flops, "tf32_tflops_achieved": flops / (scan_ms / 1e3) / 1e12,
             "tf32_peak_tflops": bf16 * 0.5}
 
