@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "scan_common.cuh"
 
 namespace {
 
@@ -95,7 +96,7 @@ namespace {
 // Device scratch one request adds to a search: its centroid-score row, query
 // row, probe lists, grouping pairs and per-probe candidate lists.
 size_t request_bytes(const soar::IndexData& ix, int k, int t) {
-  const size_t list = (size_t)std::max(k, 32) * 8;
+  const size_t list = (size_t)std::max(k <= soar::kTcWideK ? soar::scan_tc_list_len(k) : 32, k) * 8;
   return (size_t)ix.c * 4 + (size_t)(ix.d + 16) * 4 + (size_t)t * (4 + 16 + 4 + 8 + list) + (size_t)k * 12 + 256;
 }
 
