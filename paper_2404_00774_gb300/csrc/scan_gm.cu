@@ -28,8 +28,10 @@
 // score of k distinct rows, so the partition's k-th best exact score exceeds
 // a_k - delta / 2 and a row with s~ < a_k - 2 delta cannot be in the top k.
 // Per tile each epilogue thread (one query) gets the 16 group maxima from
-// the TMEM load itself (tcgen05.ld.red), sorts them (bitonic network) and
-// merges them into the 16 largest so far, raises its cut max(a_k - 2 delta,
+// the TMEM load itself (tcgen05.ld.red; from an item's third tile on, a full
+// tile is taken as 8 groups of eight rows, which halves the network), sorts
+// them (bitonic network) and merges them into the 16 largest so far (groups
+// of different sizes are still disjoint), raises its cut max(a_k - 2 delta,
 // G_q - delta) (G_q: the best bound the query's finished partitions
 // published), and appends the rows at or above the cut to the slot's
 // candidate list in shared memory: the tile's scores are parked in shared
@@ -418,13 +420,27 @@ __global__ void __launch_bounds__(kThreads, 1) scan_gm_kernel(GmParams P) {
         if (!ok) give_up();
         tc::fence_after_sync();
         uint32_t ra[32], rb[32];
-        float g[16], gu[16];                          // the tile's group maxima (groups of four rows)
+        float g[16], gu[16];                          // the tile's group maxima (groups of four or eight rows)
         const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + b * kN;
+        const int nvalid = min(kN, cur.nrows - kN * j);
+        // After an item's first two tiles the bound has mostly converged: a
+        // full tile then takes eight groups of eight rows, half the sorting
+        // and merging (groups of different sizes are still disjoint sets of
+        // distinct rows, so the bound stays valid).
+        const bool wide = j >= 2 && nvalid == kN;
         if (ok) {
+          if (wide) {
 #pragma unroll
-          for (int q4 = 0; q4 < 16; ++q4) {
-            uint32_t* r = q4 < 8 ? ra : rb;
-            tc::tmem_ld4_max(taddr + 4 * q4, r + ((4 * q4) & 31), g[q4]);
+            for (int q8 = 0; q8 < 8; ++q8) {
+              uint32_t* r = q8 < 4 ? ra : rb;
+              tc::tmem_ld8_max(taddr + 8 * q8, r + ((8 * q8) & 31), g[q8]);
+            }
+          } else {
+#pragma unroll
+            for (int q4 = 0; q4 < 16; ++q4) {
+              uint32_t* r = q4 < 8 ? ra : rb;
+              tc::tmem_ld4_max(taddr + 4 * q4, r + ((4 * q4) & 31), g[q4]);
+            }
           }
           tc::tmem_ld_wait();
         }
@@ -438,100 +454,175 @@ __global__ void __launch_bounds__(kThreads, 1) scan_gm_kernel(GmParams P) {
         // after the tile's screening, so its latency overlaps that work
         const bool refresh = active && (j & 3) == 3;
         const unsigned gload = refresh ? __ldcg(P.gbound + qid_c) : 0u;
-        const int nvalid = min(kN, cur.nrows - kN * j);
         const int32_t pr0 = (int32_t)(cur.row0 + (int64_t)kN * j);   // row-major position of the tile's first row
-        if (nvalid < kN) {                            // a short last tile: the missing rows count as -inf
+        if (wide) {
+          float gw[8];
 #pragma unroll
-          for (int c = 0; c < 32; ++c) {
-            if (c >= nvalid) ra[c] = 0xff800000u;
-            if (c + 32 >= nvalid) rb[c] = 0xff800000u;
+          for (int q8 = 0; q8 < 8; ++q8) gw[q8] = g[q8];
+          // bitonic sort of the eight group maxima, descending
+#pragma unroll
+          for (int size = 2; size <= 8; size <<= 1)
+#pragma unroll
+            for (int stride = size >> 1; stride > 0; stride >>= 1)
+#pragma unroll
+              for (int i2 = 0; i2 < 8; ++i2) {
+                const int j2 = i2 ^ stride;
+                if (j2 > i2) {
+                  const bool desc = (i2 & size) == 0;
+                  const float x = gw[i2], y = gw[j2];
+                  gw[i2] = desc ? fmaxf(x, y) : fminf(x, y);
+                  gw[j2] = desc ? fminf(x, y) : fmaxf(x, y);
+                }
+              }
+          // the list's last eight against the reversed eight, then half-cleaners
+#pragma unroll
+          for (int i2 = 8; i2 < 16; ++i2) gt[i2] = fmaxf(gt[i2], gw[15 - i2]);
+#pragma unroll
+          for (int stride = 8; stride > 0; stride >>= 1)
+#pragma unroll
+            for (int i2 = 0; i2 < 16; ++i2)
+              if ((i2 & stride) == 0) {
+                const float x = gt[i2], y = gt[i2 + stride];
+                gt[i2] = fmaxf(x, y);
+                gt[i2 + stride] = fminf(x, y);
+              }
+          if constexpr (KX > 0) {
+            ak = gt[KX - 1];
+          } else {
+            ak = INFINITY;
+#pragma unroll
+            for (int j2 = 0; j2 < kGK; ++j2)
+              if (j2 < k) ak = fminf(ak, gt[j2]);
           }
+          cut = fmaxf(ak - 2.f * dlt, gq);
+          const float cut0 = active ? cut : INFINITY;
+          uint32_t gm = 0u;                           // eight-row groups holding a row at or above the cut
 #pragma unroll
-          for (int q4 = 0; q4 < 16; ++q4) {
-            const uint32_t* r = q4 < 8 ? ra : rb;
-            const int o = (4 * q4) & 31;
-            g[q4] = fmaxf(fmaxf(__uint_as_float(r[o]), __uint_as_float(r[o + 1])),
-                          fmaxf(__uint_as_float(r[o + 2]), __uint_as_float(r[o + 3])));
-          }
-        }
+          for (int q8 = 0; q8 < 8; ++q8) gm |= (g[q8] >= cut0 ? 1u : 0u) << q8;
+          if (__any_sync(kFull, gm != 0u)) {
 #pragma unroll
-        for (int q4 = 0; q4 < 16; ++q4) gu[q4] = g[q4];
-        // bitonic sort of the group maxima, descending
+            for (int q4 = 0; q4 < 16; ++q4) {
+              const uint32_t* r = q4 < 8 ? ra : rb;
+              const int o = (4 * q4) & 31;
+              park[q4 * kM] = make_float4(__uint_as_float(r[o]), __uint_as_float(r[o + 1]),
+                                          __uint_as_float(r[o + 2]), __uint_as_float(r[o + 3]));
+            }
+            while (gm) {
+              const int q8 = __ffs(gm) - 1;
+              gm &= gm - 1u;
+              const float4 v0 = park[(2 * q8) * kM], v1 = park[(2 * q8 + 1) * kM];
+              const int c0 = 8 * q8;
+              const float vv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
 #pragma unroll
-        for (int size = 2; size <= 16; size <<= 1)
-#pragma unroll
-          for (int stride = size >> 1; stride > 0; stride >>= 1)
-#pragma unroll
-            for (int i2 = 0; i2 < 16; ++i2) {
-              const int j2 = i2 ^ stride;
-              if (j2 > i2) {
-                const bool desc = (i2 & size) == 0;
-                const float x = g[i2], y = g[j2];
-                g[i2] = desc ? fmaxf(x, y) : fminf(x, y);
-                g[j2] = desc ? fminf(x, y) : fmaxf(x, y);
+              for (int u = 0; u < 8; ++u) {
+                const bool take = vv[u] >= cut0;
+                const bool to_s = take && cnt < kCap;
+                const bool to_g = take && !to_s && wg < kGmList;
+                if (to_s) {
+                  cub[cnt * kM] = vv[u];
+                  cpos[cnt * kM] = pr0 + c0 + u;
+                }
+                if (to_g) out[wg] = Cand{vv[u] + dlt, pr0 + c0 + u};
+                ovf = ovf || (take && !to_s && !to_g);
+                cnt += to_s ? 1 : 0;
+                wg += to_g ? 1 : 0;
               }
             }
-        // the 16 largest of two descending lists: the pairwise maxima against
-        // the reversed list form a bitonic sequence, which half-cleaners sort
-#pragma unroll
-        for (int i2 = 0; i2 < 16; ++i2) gt[i2] = fmaxf(gt[i2], g[15 - i2]);
-#pragma unroll
-        for (int stride = 8; stride > 0; stride >>= 1)
-#pragma unroll
-          for (int i2 = 0; i2 < 16; ++i2)
-            if ((i2 & stride) == 0) {
-              const float x = gt[i2], y = gt[i2 + stride];
-              gt[i2] = fmaxf(x, y);
-              gt[i2 + stride] = fminf(x, y);
-            }
-        if constexpr (KX > 0) {
-          ak = gt[KX - 1];
-        } else {                                      // gt[k - 1] as the smallest of the first k: gt stays in registers
-          ak = INFINITY;
-#pragma unroll
-          for (int j2 = 0; j2 < kGK; ++j2)
-            if (j2 < k) ak = fminf(ak, gt[j2]);
-        }
-        cut = fmaxf(ak - 2.f * dlt, gq);              // s~ + dlt < max(L_k, G_q)  <=>  s~ < cut
-        const float cut0 = active ? cut : INFINITY;
-        uint32_t gm = 0u;                             // groups holding a row at or above the cut
-#pragma unroll
-        for (int q4 = 0; q4 < 16; ++q4) gm |= (gu[q4] >= cut0 ? 1u : 0u) << q4;
-        // past the partition's end nothing is a candidate, not even while the
-        // cut is still -inf (the padding rows read as -inf)
-        if (nvalid < kN) gm &= (1u << ((nvalid + 3) >> 2)) - 1u;
-        if (__any_sync(kFull, gm != 0u)) {
-          // park the tile's scores, then one trip per surviving group of the
-          // lane: its four scores back from shared memory, the rows at or
-          // above the cut appended (predicated, no nested branches)
-#pragma unroll
-          for (int q4 = 0; q4 < 16; ++q4) {
-            const uint32_t* r = q4 < 8 ? ra : rb;
-            const int o = (4 * q4) & 31;
-            park[q4 * kM] = make_float4(__uint_as_float(r[o]), __uint_as_float(r[o + 1]),
-                                        __uint_as_float(r[o + 2]), __uint_as_float(r[o + 3]));
           }
-          while (gm) {
-            const int q4 = __ffs(gm) - 1;
-            gm &= gm - 1u;
-            const float4 v = park[q4 * kM];
-            const int c0 = 4 * q4;
-            const float vv[4] = {v.x, v.y, v.z, v.w};
+        } else {
+          if (nvalid < kN) {                            // a short last tile: the missing rows count as -inf
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              // to the shared list while it has room, then straight to the
-              // pair's global list (stores only, nothing read back)
-              const bool take = vv[u] >= cut0 && c0 + u < nvalid;
-              const bool to_s = take && cnt < kCap;
-              const bool to_g = take && !to_s && wg < kGmList;
-              if (to_s) {
-                cub[cnt * kM] = vv[u];
-                cpos[cnt * kM] = pr0 + c0 + u;
+            for (int c = 0; c < 32; ++c) {
+              if (c >= nvalid) ra[c] = 0xff800000u;
+              if (c + 32 >= nvalid) rb[c] = 0xff800000u;
+            }
+#pragma unroll
+            for (int q4 = 0; q4 < 16; ++q4) {
+              const uint32_t* r = q4 < 8 ? ra : rb;
+              const int o = (4 * q4) & 31;
+              g[q4] = fmaxf(fmaxf(__uint_as_float(r[o]), __uint_as_float(r[o + 1])),
+                            fmaxf(__uint_as_float(r[o + 2]), __uint_as_float(r[o + 3])));
+            }
+          }
+#pragma unroll
+          for (int q4 = 0; q4 < 16; ++q4) gu[q4] = g[q4];
+          // bitonic sort of the group maxima, descending
+#pragma unroll
+          for (int size = 2; size <= 16; size <<= 1)
+#pragma unroll
+            for (int stride = size >> 1; stride > 0; stride >>= 1)
+#pragma unroll
+              for (int i2 = 0; i2 < 16; ++i2) {
+                const int j2 = i2 ^ stride;
+                if (j2 > i2) {
+                  const bool desc = (i2 & size) == 0;
+                  const float x = g[i2], y = g[j2];
+                  g[i2] = desc ? fmaxf(x, y) : fminf(x, y);
+                  g[j2] = desc ? fminf(x, y) : fmaxf(x, y);
+                }
               }
-              if (to_g) out[wg] = Cand{vv[u] + dlt, pr0 + c0 + u};
-              ovf = ovf || (take && !to_s && !to_g);
-              cnt += to_s ? 1 : 0;
-              wg += to_g ? 1 : 0;
+          // the 16 largest of two descending lists: the pairwise maxima against
+          // the reversed list form a bitonic sequence, which half-cleaners sort
+#pragma unroll
+          for (int i2 = 0; i2 < 16; ++i2) gt[i2] = fmaxf(gt[i2], g[15 - i2]);
+#pragma unroll
+          for (int stride = 8; stride > 0; stride >>= 1)
+#pragma unroll
+            for (int i2 = 0; i2 < 16; ++i2)
+              if ((i2 & stride) == 0) {
+                const float x = gt[i2], y = gt[i2 + stride];
+                gt[i2] = fmaxf(x, y);
+                gt[i2 + stride] = fminf(x, y);
+              }
+          if constexpr (KX > 0) {
+            ak = gt[KX - 1];
+          } else {                                      // gt[k - 1] as the smallest of the first k: gt stays in registers
+            ak = INFINITY;
+#pragma unroll
+            for (int j2 = 0; j2 < kGK; ++j2)
+              if (j2 < k) ak = fminf(ak, gt[j2]);
+          }
+          cut = fmaxf(ak - 2.f * dlt, gq);              // s~ + dlt < max(L_k, G_q)  <=>  s~ < cut
+          const float cut0 = active ? cut : INFINITY;
+          uint32_t gm = 0u;                             // groups holding a row at or above the cut
+#pragma unroll
+          for (int q4 = 0; q4 < 16; ++q4) gm |= (gu[q4] >= cut0 ? 1u : 0u) << q4;
+          // past the partition's end nothing is a candidate, not even while the
+          // cut is still -inf (the padding rows read as -inf)
+          if (nvalid < kN) gm &= (1u << ((nvalid + 3) >> 2)) - 1u;
+          if (__any_sync(kFull, gm != 0u)) {
+            // park the tile's scores, then one trip per surviving group of the
+            // lane: its four scores back from shared memory, the rows at or
+            // above the cut appended (predicated, no nested branches)
+#pragma unroll
+            for (int q4 = 0; q4 < 16; ++q4) {
+              const uint32_t* r = q4 < 8 ? ra : rb;
+              const int o = (4 * q4) & 31;
+              park[q4 * kM] = make_float4(__uint_as_float(r[o]), __uint_as_float(r[o + 1]),
+                                          __uint_as_float(r[o + 2]), __uint_as_float(r[o + 3]));
+            }
+            while (gm) {
+              const int q4 = __ffs(gm) - 1;
+              gm &= gm - 1u;
+              const float4 v = park[q4 * kM];
+              const int c0 = 4 * q4;
+              const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                // to the shared list while it has room, then straight to the
+                // pair's global list (stores only, nothing read back)
+                const bool take = vv[u] >= cut0 && c0 + u < nvalid;
+                const bool to_s = take && cnt < kCap;
+                const bool to_g = take && !to_s && wg < kGmList;
+                if (to_s) {
+                  cub[cnt * kM] = vv[u];
+                  cpos[cnt * kM] = pr0 + c0 + u;
+                }
+                if (to_g) out[wg] = Cand{vv[u] + dlt, pr0 + c0 + u};
+                ovf = ovf || (take && !to_s && !to_g);
+                cnt += to_s ? 1 : 0;
+                wg += to_g ? 1 : 0;
+              }
             }
           }
         }

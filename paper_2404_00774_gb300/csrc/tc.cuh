@@ -209,6 +209,15 @@ __device__ __forceinline__ void tmem_ld4_max(uint32_t taddr, uint32_t* r, float&
                : "memory");
 }
 
+// Eight columns of this warp's 32 TMEM lanes and their maximum.
+__device__ __forceinline__ void tmem_ld8_max(uint32_t taddr, uint32_t* r, float& mx) {
+  asm volatile("tcgen05.ld.red.sync.aligned.32x32b.x8.max.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, %8, [%9];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                 "=f"(mx)
+               : "r"(taddr)
+               : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 }  // namespace tc
