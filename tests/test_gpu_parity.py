@@ -128,7 +128,9 @@ def test_soar_assign_many_tied_centroids(soar):
 
 
 def test_soar_assign_glove_shaped_slice(soar):
-    # d = 100 (the Glove shape): many 128-point tiles, several centroid tiles
+    # d = 100 (the Glove shape): many 128-point tiles; c = 256 is one
+    # primary-pass tile of 256 centroids and two spill-pass tiles of 128 (the
+    # primary pass across several tiles runs at c = 2 000 in test_gpu_at_size.py)
     w = synth.WORKLOADS["glove"]
     mix = synth.mixture_for(w)
     X = mix.sample(12_000, 7)
