@@ -13,13 +13,13 @@
 //
 // Pipelining.  The producer publishes the next item's description before it
 // streams the current item's tiles and never waits for an item boundary, so
-// the tile ring stays full across items.  The epilogue loads the next item's
-// query ids at the start of the current item, their norms and bounds after
-// its first tile (prefetching their rows into L2), and copies the rows into
-// the A operand as soon as the current item's last tile has arrived (its
-// MMAs, the last readers of A, have then completed), while it screens that
-// tile; the MMA issuer starts the next item while the epilogue writes out
-// the current item's candidates.
+// the tile ring stays full across items.  The A operand is double-buffered
+// (items alternate): the epilogue loads the next item's query ids at the
+// start of the current item and, after its first tile (the MMAs of the item
+// before, the last readers of the other buffer, have then completed), copies
+// their rows into the other buffer, which it hands to the MMA issuer two
+// tiles later; the MMA issuer runs on into the next item while the epilogue
+// finishes the current one.
 //
 // Screening (exactness as in the tensor-core scan of scan_tc.cu): a screened
 // score s~ lies within delta / 2 of the fp32 dot product, delta = dscale *
@@ -67,6 +67,7 @@ constexpr int kNB = 4;         // TMEM accumulators (kN columns each)
 constexpr int kRing = 4;       // item descriptions in flight
 constexpr int kGK = 16;        // group maxima kept per query (k <= kGK)
 constexpr int kCap = 32;       // candidate rows held per query slot in shared memory
+constexpr int kStageAt = 2;    // the next item's A buffer is released after this many tiles of the current one
 
 struct GmParams {
   IvfWork work;
@@ -132,11 +133,11 @@ __global__ void __launch_bounds__(kThreads, 1) scan_gm_kernel(GmParams P) {
   const int k = KX > 0 ? KX : P.k;
   const uint32_t sbo = (uint32_t)kp * 8u * es;         // bytes between 8-row groups
   const uint32_t a_part = (uint32_t)kM * kp * es;      // one A part (bf16: hi or lo)
-  const uint32_t a_bytes = (es == 4 ? 1u : 2u) * a_part;   // the A operand
+  const uint32_t a_bytes = (es == 4 ? 1u : 2u) * a_part;   // one A operand buffer
   const uint32_t b_bytes = (uint32_t)kN * kp * es;
   const char* rows = static_cast<const char*>(P.rows);
-  unsigned char* sA = base;
-  unsigned char* sB = base + a_bytes;
+  unsigned char* sA = base;                            // two A operand buffers (items alternate)
+  unsigned char* sB = base + 2 * a_bytes;
   // a tile's scores parked per query slot as 16 float4 groups ([group][kM],
   // so that a warp's 32 lanes write 512 consecutive bytes), then the
   // candidates per query slot ([entry][kM]: 32 lanes, 32 distinct banks):
@@ -144,8 +145,9 @@ __global__ void __launch_bounds__(kThreads, 1) scan_gm_kernel(GmParams P) {
   float4* park_s = reinterpret_cast<float4*>(sB + (size_t)S * b_bytes);
   float* list_s = reinterpret_cast<float*>(park_s + 16 * kM);
   uint64_t* bars = reinterpret_cast<uint64_t*>(list_s + 2 * kCap * kM);
-  // bars: full[S], empty[S], tfull[kNB], tempty[kNB], dfull[kRing], dempty[kRing], aready
+  // bars: full[S], empty[S], tfull[kNB], tempty[kNB], dfull[kRing], dempty[kRing], aready[2], agone[2]
   __shared__ Item ring_s[kRing];
+  __shared__ uint32_t abuf_s[2];                       // A buffer of the tile handed to the MMA issuer
   __shared__ uint32_t tmem_base_s;
   __shared__ int abort_s;
   __shared__ int issued_s, consumed_s, committed_s;
@@ -157,7 +159,10 @@ __global__ void __launch_bounds__(kThreads, 1) scan_gm_kernel(GmParams P) {
   auto tempty = [&](int b) { return tc::smem_u32(&bars[2 * S + kNB + b]); };
   auto dfull = [&](int r) { return tc::smem_u32(&bars[2 * S + 2 * kNB + r]); };
   auto dempty = [&](int r) { return tc::smem_u32(&bars[2 * S + 2 * kNB + kRing + r]); };
-  auto aready = [&]() { return tc::smem_u32(&bars[2 * S + 2 * kNB + 2 * kRing]); };
+  auto aready = [&](int a) { return tc::smem_u32(&bars[2 * S + 2 * kNB + 2 * kRing + a]); };
+  // the gate has seen buffer a's staged item (so the epilogue never readies
+  // a buffer twice before the gate has waited once)
+  auto agone = [&](int a) { return tc::smem_u32(&bars[2 * S + 2 * kNB + 2 * kRing + 2 + a]); };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -172,7 +177,10 @@ __global__ void __launch_bounds__(kThreads, 1) scan_gm_kernel(GmParams P) {
       tc::bar_init(dfull(r), 1);
       tc::bar_init(dempty(r), 5);                      // the gate and the four epilogue warps
     }
-    tc::bar_init(aready(), 4);
+    tc::bar_init(aready(0), 4);
+    tc::bar_init(aready(1), 4);
+    tc::bar_init(agone(0), 1);
+    tc::bar_init(agone(1), 1);
     tc::bar_init_fence();
     abort_s = 0;
     issued_s = consumed_s = committed_s = 0;
@@ -242,7 +250,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_gm_kernel(GmParams P) {
       const uint32_t s = T % S, b = T % kNB;
       if (lane == 0) {
         tc::fence_after_sync();
-        const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB) + s * b_bytes;
+        const uint32_t a0 = tc::smem_u32(sA) + abuf_s[T & 1] * a_bytes, b0 = tc::smem_u32(sB) + s * b_bytes;
         const int steps = (int)(kp * es / 32);       // one MMA per 32 bytes of K (2 core matrices)
         for (int j = 0; j < steps; ++j) {
           const uint64_t ad = tc::smem_desc(a0 + j * 256, 128, sbo), bd = tc::smem_desc(b0 + j * 256, 128, sbo);
@@ -274,7 +282,10 @@ __global__ void __launch_bounds__(kThreads, 1) scan_gm_kernel(GmParams P) {
           const Item d = ring_s[r];
           nt = d.p < 0 ? -1 : (d.ng + 7) / 8;
         }
-        if (ok && nt >= 0) ok = tc::bar_wait(aready(), i & 1, abort_v, lim);
+        if (ok && nt >= 0) {
+          ok = tc::bar_wait(aready(i & 1), (i >> 1) & 1, abort_v, lim);
+          if (ok) tc::bar_arrive(agone(i & 1));
+        }
         if (!ok) give_up();
       }
       ok = __shfl_sync(kFull, ok, 0);
@@ -290,6 +301,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_gm_kernel(GmParams P) {
           ok2 = tc::bar_wait(full(s), ph, abort_v, lim) && tc::bar_wait(tempty(b), tph ^ 1, abort_v, lim);
           if (!ok2) give_up();
           else consumed_s = (int)(T + 1);
+          abuf_s[T & 1] = (uint32_t)(i & 1);
           tc::fence_before_sync();
         }
         ok2 = __shfl_sync(kFull, ok2, 0);
@@ -306,9 +318,9 @@ __global__ void __launch_bounds__(kThreads, 1) scan_gm_kernel(GmParams P) {
     const int jq = 4 * lane + (warp & 3);             // the item's query in that slot
     const int chunks = (int)(kp * es / 16);
     const int64_t qrow = (int64_t)kp * (es == 4 ? 1 : 2);   // elements per query row of Qa
-    // stage query qi (or zeros for an idle slot) into row m of the A operand
-    auto stage_row = [&](bool use, int64_t qi) {
-      unsigned char* arow = sA + (m >> 3) * (kp * 8 * es) + (m & 7) * 16;
+    // stage query qi (or zeros for an idle slot) into row m of A buffer ab
+    auto stage_row = [&](int ab, bool use, int64_t qi) {
+      unsigned char* arow = sA + ab * a_bytes + (m >> 3) * (kp * 8 * es) + (m & 7) * 16;
       if (use) {
         const ET* q = static_cast<const ET*>(P.Qa) + qi * qrow;
         for (int c = 0; c < chunks; ++c) tc::cp_async16(tc::smem_u32(arow + c * 128), q + (16 / es) * c);
@@ -321,11 +333,11 @@ __global__ void __launch_bounds__(kThreads, 1) scan_gm_kernel(GmParams P) {
         }
       }
     };
-    auto release_a = [&]() {
+    auto release_a = [&](int ab) {
       tc::cp_async_wait_all();
       tc::fence_async_smem();
       __syncwarp();
-      if (lane == 0) tc::bar_arrive(aready());
+      if (lane == 0) tc::bar_arrive(aready(ab));
     };
     float4* park = park_s + m;                        // [16][kM] the tile's scores by group
     float* cub = list_s + m;                          // [kCap][kM] screened scores
@@ -346,18 +358,19 @@ __global__ void __launch_bounds__(kThreads, 1) scan_gm_kernel(GmParams P) {
           gb_c = __ldcg(P.gbound + qid_c);
         }
         pmax_c = P.pmax[cur.p];
-        stage_row(use, qid_c);
-        release_a();
+        stage_row(0, use, qid_c);
+        release_a(0);
       }
     } else {
       give_up();
     }
     uint32_t T = 0;
     for (int i = 0; cur.p >= 0 && !abort_s; ++i) {
-      // the next item: its description and its queries' ids now; after the
-      // first tile its queries' norms and bounds, and their rows prefetched
-      // into L2; at the last tile (all of this item's MMAs have completed,
-      // so the A operand is free) the rows copied into A
+      // the next item: its description and its queries' ids now; after this
+      // item's first tile (item i - 1's MMAs, the last readers of the other
+      // A buffer, have then completed) its queries' norms and bounds, and
+      // their rows copied into that buffer, released to the MMA issuer a few
+      // tiles later
       Item nxt{};
       nxt.p = -1;
       if (tc::bar_wait(dfull((i + 1) % kRing), ((i + 1) / kRing) & 1, abort_v, lim)) nxt = ring_s[(i + 1) % kRing];
@@ -371,21 +384,24 @@ __global__ void __launch_bounds__(kThreads, 1) scan_gm_kernel(GmParams P) {
       int64_t qid_n = 0;
       unsigned gb_n = 0u;
       float qn_n = 0.f;
-      bool fetched = false, staged = false;
-      auto fetch_next = [&]() {
-        if (fetched) return;
-        fetched = true;
-        if (!use_n) return;
-        qid_n = pv_n / P.work.tmax;
-        qn_n = P.qnorm[qid_n];
-        gb_n = __ldcg(P.gbound + qid_n);
-        tc::bulk_prefetch_l2(static_cast<const char*>(P.Qa) + qid_n * qrow * (int64_t)es, (uint32_t)(qrow * es));
-      };
+      bool staged = false, released = false;
       auto stage_next = [&]() {
         if (staged) return;
-        fetch_next();
         staged = true;
-        if (has_next) stage_row(use_n, qid_n);
+        if (!has_next) return;
+        if (use_n) {
+          qid_n = pv_n / P.work.tmax;
+          qn_n = P.qnorm[qid_n];
+          gb_n = __ldcg(P.gbound + qid_n);
+        }
+        stage_row((i + 1) & 1, use_n, qid_n);
+      };
+      auto release_next = [&]() {
+        if (released || !has_next) return;
+        released = true;
+        // buffer (i + 1) & 1 last held item i - 1: the gate must have seen it
+        if (i >= 1 && !tc::bar_wait(agone((i + 1) & 1), ((i - 1) >> 1) & 1, abort_v, lim)) give_up();
+        release_a((i + 1) & 1);
       };
 
       // ---- the current item
@@ -448,8 +464,8 @@ __global__ void __launch_bounds__(kThreads, 1) scan_gm_kernel(GmParams P) {
         __syncwarp();
         if (lane == 0) tc::bar_arrive(tempty(b));
         if (!ok) break;
-        if (j == 1) fetch_next();
-        if (j == nt - 1) stage_next();
+        if (j == 0) stage_next();
+        if (j == kStageAt) release_next();
         // every fourth tile refresh G_q; the load is issued here and used
         // after the tile's screening, so its latency overlaps that work
         const bool refresh = active && (j & 3) == 3;
@@ -631,8 +647,8 @@ __global__ void __launch_bounds__(kThreads, 1) scan_gm_kernel(GmParams P) {
           cut = fmaxf(cut, gq);
         }
       }
-      stage_next();                                   // an item without tiles
-      if (has_next) release_a();
+      stage_next();                                   // items with fewer tiles
+      release_next();
       if (active && !abort_s) {
         const int64_t e = cur.e0 + jq;
         flush(cut);                                   // the candidates still at or above the final cut
@@ -669,10 +685,10 @@ __global__ void __launch_bounds__(kThreads, 1) scan_gm_kernel(GmParams P) {
 }
 
 size_t gm_smem_bytes(int kp, int stages, int es) {
-  // the A operand takes kM * kp * 4 bytes (fp32, or bf16 hi and lo); the
+  // each of the two A buffers takes kM * kp * 4 bytes (fp32, or bf16 hi and lo); the
   // parked tile kN * kM * 4, the candidate lists 2 * kCap * kM * 4
-  return 1024 + (size_t)kM * kp * 4 + (size_t)stages * kN * kp * es + (size_t)kN * kM * 4 +
-         (size_t)2 * kCap * kM * 4 + (size_t)(2 * stages + 2 * kNB + 2 * kRing + 1) * 8;
+  return 1024 + (size_t)2 * kM * kp * 4 + (size_t)stages * kN * kp * es + (size_t)kN * kM * 4 +
+         (size_t)2 * kCap * kM * 4 + (size_t)(2 * stages + 2 * kNB + 2 * kRing + 4) * 8;
 }
 
 int gm_pick_stages(int kp, int es) {
