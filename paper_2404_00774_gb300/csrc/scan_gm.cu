@@ -517,11 +517,12 @@ __global__ void __launch_bounds__(kThreads, 1) scan_gm_kernel(GmParams P) {
           for (int q8 = 0; q8 < 8; ++q8) gm |= (g[q8] >= cut0 ? 1u : 0u) << q8;
           if (__any_sync(kFull, gm != 0u)) {
 #pragma unroll
-            for (int q4 = 0; q4 < 16; ++q4) {
+            for (int q4 = 0; q4 < 16; ++q4) {         // only the lane's surviving groups are parked
               const uint32_t* r = q4 < 8 ? ra : rb;
               const int o = (4 * q4) & 31;
-              park[q4 * kM] = make_float4(__uint_as_float(r[o]), __uint_as_float(r[o + 1]),
-                                          __uint_as_float(r[o + 2]), __uint_as_float(r[o + 3]));
+              if ((gm >> (q4 >> 1)) & 1u)
+                park[q4 * kM] = make_float4(__uint_as_float(r[o]), __uint_as_float(r[o + 1]),
+                                            __uint_as_float(r[o + 2]), __uint_as_float(r[o + 3]));
             }
             while (gm) {
               const int q8 = __ffs(gm) - 1;
@@ -611,11 +612,12 @@ __global__ void __launch_bounds__(kThreads, 1) scan_gm_kernel(GmParams P) {
             // lane: its four scores back from shared memory, the rows at or
             // above the cut appended (predicated, no nested branches)
 #pragma unroll
-            for (int q4 = 0; q4 < 16; ++q4) {
+            for (int q4 = 0; q4 < 16; ++q4) {         // only the lane's surviving groups are parked
               const uint32_t* r = q4 < 8 ? ra : rb;
               const int o = (4 * q4) & 31;
-              park[q4 * kM] = make_float4(__uint_as_float(r[o]), __uint_as_float(r[o + 1]),
-                                          __uint_as_float(r[o + 2]), __uint_as_float(r[o + 3]));
+              if ((gm >> q4) & 1u)
+                park[q4 * kM] = make_float4(__uint_as_float(r[o]), __uint_as_float(r[o + 1]),
+                                            __uint_as_float(r[o + 2]), __uint_as_float(r[o + 3]));
             }
             while (gm) {
               const int q4 = __ffs(gm) - 1;
