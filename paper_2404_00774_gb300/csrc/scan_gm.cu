@@ -34,9 +34,9 @@
 // of different sizes are still disjoint), raises its cut max(a_k - 2 delta,
 // G_q - delta) (G_q: the best bound the query's finished partitions
 // published), and appends the rows at or above the cut to the slot's
-// candidate list in shared memory: the tile's scores are parked in shared
-// memory and only the groups whose maximum reaches the cut are read back,
-// one loop trip per such group.  The cost of a tile barely depends on how
+// candidate list in shared memory: each thread parks in shared memory only
+// its groups whose maximum reaches the cut and reads them back, one loop
+// trip per such group.  The cost of a tile barely depends on how
 // many rows survive, so no warp waits long on its lane with the most
 // survivors.  Once a slot's shared list is full its further candidates go
 // straight to the pair's list in global memory; at the end of an item the
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_gm_kernel(GmParams P) {
   const char* rows = static_cast<const char*>(P.rows);
   unsigned char* sA = base;                            // two A operand buffers (items alternate)
   unsigned char* sB = base + 2 * a_bytes;
-  // a tile's scores parked per query slot as 16 float4 groups ([group][kM],
+  // a tile's surviving groups parked per query slot as float4s ([group][kM],
   // so that a warp's 32 lanes write 512 consecutive bytes), then the
   // candidates per query slot ([entry][kM]: 32 lanes, 32 distinct banks):
   // scores, then padded row positions
@@ -608,9 +608,9 @@ __global__ void __launch_bounds__(kThreads, 1) scan_gm_kernel(GmParams P) {
           // cut is still -inf (the padding rows read as -inf)
           if (nvalid < kN) gm &= (1u << ((nvalid + 3) >> 2)) - 1u;
           if (__any_sync(kFull, gm != 0u)) {
-            // park the tile's scores, then one trip per surviving group of the
-            // lane: its four scores back from shared memory, the rows at or
-            // above the cut appended (predicated, no nested branches)
+            // park the lane's surviving groups, then one trip per such group:
+            // its four scores back from shared memory, the rows at or above
+            // the cut appended (predicated, no nested branches)
 #pragma unroll
             for (int q4 = 0; q4 < 16; ++q4) {         // only the lane's surviving groups are parked
               const uint32_t* r = q4 < 8 ? ra : rb;
@@ -688,7 +688,7 @@ __global__ void __launch_bounds__(kThreads, 1) scan_gm_kernel(GmParams P) {
 
 size_t gm_smem_bytes(int kp, int stages, int es) {
   // each of the two A buffers takes kM * kp * 4 bytes (fp32, or bf16 hi and lo); the
-  // parked tile kN * kM * 4, the candidate lists 2 * kCap * kM * 4
+  // parking area kN * kM * 4, the candidate lists 2 * kCap * kM * 4
   return 1024 + (size_t)2 * kM * kp * 4 + (size_t)stages * kN * kp * es + (size_t)kN * kM * 4 +
          (size_t)2 * kCap * kM * 4 + (size_t)(2 * stages + 2 * kNB + 2 * kRing + 4) * 8;
 }
