@@ -223,8 +223,9 @@ SCAN_KERNEL = "scan_gm_kernel"        # the partition scan for k <= 16 (csrc/sca
 
 def kernel_hash():
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_2404_00774_gb300", "csrc", "scan_gm.cu"), "rb") as f:
-        h.update(f.read())
+    for name in ("scan_gm.cu", "scan_common.cuh", "tc.cuh"):
+        with open(os.path.join(ROOT, "paper_2404_00774_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
@@ -250,7 +251,7 @@ def scan_roofline(w, nq, k, t, ix, Qd, sb, scan_ms, hbm, bf16, peak_src):
     per row, plus the queries (4d bytes each) and the results (12 bytes per
     neighbour).  The bytes the kernel's own schedule adds (a partition
     re-read for each further chunk of 128 of its queries, the per-pair
-    candidate lists, at most 64 entries of 8 bytes each) are reported beside
+    candidate lists, at most 128 entries of 8 bytes each) are reported beside
     them, not counted."""
     import torch
     offsets = ix.offsets()
@@ -271,7 +272,7 @@ def scan_roofline(w, nq, k, t, ix, Qd, sb, scan_ms, hbm, bf16, peak_src):
             "ms_per_launch": scan_ms, "algorithmic_bytes": bytes_alg,
             "algorithmic_rule": "distinct probed partitions x rows x (4d + 4) + queries + results",
             "schedule_bytes": {"rows_rereads": (rows_sched - rows_once) * kp * 4,
-                               "candidate_list_capacity": nq * t * 8 * 64, "row_bytes_padded_k": kp * 4},
+                               "candidate_list_capacity": nq * t * 8 * 128, "row_bytes_padded_k": kp * 4},
             "algorithmic_flops": flops, "tf32_tflops_achieved": flops / (scan_ms / 1e3) / 1e12,
             "tf32_peak_tflops": bf16 * 0.5}
 
@@ -960,9 +961,11 @@ def run_ours(args):
     for name in built:
         tt = results[name]["t"]
         if name != "soar" and tt:
-            ms = statistics.mean(step_times(built[name][0], tt, args.steps, args.warmup))
+            ms = statistics.mean(step_times(built[name][0], tt, args.steps, args.warmup, stage=True))
+            st = sb.soar_stage_times()
             results[name]["qps"] = nq / (ms / 1e3)
             results[name]["ms_per_step"] = ms
+            results[name]["stages_ms_per_step"] = {kk: v[0] / max(1, v[1]) for kk, v in st.items()}
 
     # ---- the timed region
     for _ in range(args.warmup):

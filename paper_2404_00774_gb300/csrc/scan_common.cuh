@@ -80,7 +80,7 @@ bool scan_tc_search(const IndexData& ix, const IvfWork& work, int max_items, con
 int scan_tc_max_k(const IndexData& ix);
 // Candidate-list length per pair slot of the group-maxima scan (scan_gm.cu),
 // which takes k <= 16 when its shared memory fits the row width.
-constexpr int kGmList = 64;
+constexpr int kGmList = 128;
 bool scan_gm_usable(const IndexData& ix, int k);
 // Launches it (after the caller cleared the headers, set the bounds to -inf
 // and zeroed the work counter); lists [pairs][kGmList].
