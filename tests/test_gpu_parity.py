@@ -355,13 +355,14 @@ def test_search_short_partitions_few_probes(soar, k, t):
 
 
 def test_search_equal_rows_overflow_candidate_lists(soar):
-    # 48 identical rows in one partition tie exactly for queries sitting on
-    # them: more candidates than a screened list holds, so the exact rescan of
-    # that partition decides, and ties must still go to the lower ids
+    # 200 identical rows in one partition tie exactly for queries sitting on
+    # them: more candidates than a screened list holds (160 entries for
+    # k <= 16, 32 for k <= 32), so the exact rescan of that partition
+    # decides, and ties must still go to the lower ids
     rng = np.random.default_rng(31)
     X = rng.standard_normal((3000, 40)).astype(np.float32)
     X /= np.linalg.norm(X, axis=1, keepdims=True)
-    X[100:148] = X[100]
+    X[100:300] = X[100]
     Q = rng.standard_normal((20, 40)).astype(np.float32)
     Q[:6] = X[100] + 0.01 * rng.standard_normal((6, 40)).astype(np.float32)
     Q /= np.linalg.norm(Q, axis=1, keepdims=True)
@@ -369,7 +370,7 @@ def test_search_equal_rows_overflow_candidate_lists(soar):
     A = oracle.soar_assign(X, C, 1.0, 1)
     off, ids = oracle.build_ivf(A, 16)
     ix = soar.soar_index_build(_t(X), _t(C), _t(A))
-    for k, t in [(10, 2), (32, 3), (1, 1)]:
+    for k, t in [(10, 2), (16, 3), (32, 3), (1, 1)]:
         gi, gs = soar.soar_search(ix, _t(Q), k, t)
         wi, ws = oracle.ivf_search(Q, X, C, off, ids, k, t)
         gi = gi.cpu().numpy()
@@ -377,6 +378,29 @@ def test_search_equal_rows_overflow_candidate_lists(soar):
         np.testing.assert_array_equal(gi[:6, :min(k, 10)], wi[:6, :min(k, 10)])
     soar.soar_check_device()
     ix.close()
+
+
+@pytest.mark.parametrize("k", [10, 16])
+def test_search_fp32_rows_past_the_group_maxima_scan(soar, k):
+    # d = 130 (136 fp32 columns): two A buffers of the group-maxima scan no
+    # longer fit in shared memory, so k <= 16 runs on the single-buffer scan
+    # (register top-k); ragged sizes, parity with the oracle
+    mix = synth.Mixture(130, 20, "isotropic", 0.3, param_seed=61)
+    X = mix.sample(6001, seed=62)
+    Q = mix.sample(301, seed=63)
+    C = oracle.kmeans(X, synth.init_indices(6001, 24, seed=64), 3)
+    A = oracle.soar_assign(X, C, 1.0, 1)
+    off, ids = oracle.build_ivf(A, 24)
+    ix = soar.soar_index_build(_t(X), _t(C), _t(A))
+    try:
+        gi, gs = soar.soar_search(ix, _t(Q), k, 4)
+        wi, ws = oracle.ivf_search(Q, X, C, off, ids, k, 4)
+        gi, gs = gi.cpu().numpy(), gs.cpu().numpy()
+        assert topk_mismatches(gi, wi, ws, _exact(X, Q)) == []
+        mx, mean = score_errors(gi, gs, _exact(X, Q))
+        assert mx < 1e-5, (mx, mean)
+    finally:
+        ix.close()
 
 
 @pytest.mark.parametrize("k,t", [(33, 4), (64, 17), (128, 6)])
