@@ -47,6 +47,7 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS, FALLBACK_BF16_TFLOPS = 6800.0, 1900.0
 SMS, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 METRIC = "QPS at recall@10>=0.9"
+PROBE_TOP = 32           # top centroid scores in the probe features (the tensor-core selection keeps <= 32)
 RECALL_TARGET = 0.9
 
 
@@ -382,23 +383,24 @@ def learned_probe_arm(sb, ix, mix, w, Xd, Qd, truth, k, soar_arm, step_times, n_
     Qcal = torch.from_numpy(mix.sample(4000, 305)).to(Qd.device)
     truth_tr = torch.cat([sb.soar_exact_mips(Xd, Qtr[i:i + 10000], k)[0] for i in range(0, n_train, 10000)])
     truth_cal = sb.soar_exact_mips(Xd, Qcal, k)[0]
-    Ztr = sb.soar_probe_features(ix, Qtr, 64)
+    Ztr = sb.soar_probe_features(ix, Qtr, PROBE_TOP)
     labels = sb.soar_probe_labels(ix, Qtr, truth_tr, RECALL_TARGET)
     params, losses = probe.train(ix, Ztr, labels, hidden=256, steps=steps, batch=4096, lr=1e-3, bf16=True)
-    # predictions are capped at the 99th percentile of the training labels: the
-    # few queries whose neighbours sit in far-ranked partitions would otherwise
-    # set the batch's probe count for everyone
-    t_cap = int(torch.quantile(labels.float(), 0.99).item())
-    Zcal = sb.soar_probe_features(ix, Qcal, 64)
+    # predictions are capped at the 99th percentile of the training labels
+    # (the few queries whose neighbours sit in far-ranked partitions would
+    # otherwise set the batch's probe count for everyone) and at the top
+    # partitions the features carry, which are the ones the search probes
+    t_cap = min(PROBE_TOP, int(torch.quantile(labels.float(), 0.99).item()))
+    Zcal = sb.soar_probe_features(ix, Qcal, PROBE_TOP)
     alpha = probe.calibrate_alpha(ix, params, 256, Zcal, Qcal, truth_cal, k, t_cap)
     train_s = time.perf_counter() - t0
     # timed: features + MLP + search, per step, the whole query batch
     import statistics as st
 
     def step():
-        Z = sb.soar_probe_features(ix, Qd, 64)
-        t = sb.soar_mlp_predict_probes(params, Z.shape[1], 256, Z, alpha, t_cap, True)
-        return sb.soar_search(ix, Qd, k, int(t.max()), t_per_query=t), t
+        # one call: the top PROBE_TOP selection with scores, features, network, scan
+        ids_, sc_, t = sb.soar_search_learned(ix, Qd, k, PROBE_TOP, params, 256, alpha, t_cap, True)
+        return (ids_, sc_), t
 
     for _ in range(3):
         step()
@@ -417,7 +419,8 @@ def learned_probe_arm(sb, ix, mix, w, Xd, Qd, truth, k, soar_arm, step_times, n_
     return {"recall": rec, "mean_t": float(t.float().mean()), "max_t": int(t.max()), "alpha": alpha, "t_cap": t_cap,
             "qps": Qd.shape[0] / (ms / 1e3), "ms_per_step": ms, "fixed_t": soar_arm["t"],
             "fixed_t_qps": soar_arm.get("qps"), "train_queries": n_train, "train_steps": steps,
-            "final_train_loss": losses[-1], "setup_s": train_s}
+            "final_train_loss": losses[-1], "setup_s": train_s,
+            "path": f"soar_search_learned: top-{PROBE_TOP} selection with scores, features, network, scan in one call"}
 
 
 def serving_arm(sb, ix, Q, k, rates=(100_000, 300_000, 1_000_000, 3_000_000), n_req=50_000):
@@ -731,20 +734,19 @@ def precision_at_size(sb, dev, steps, warmup, n_train=1_000_000, n_test=10_000, 
     torch.cuda.synchronize()
     label_gt_s = time.perf_counter() - t1
     truth_cal = sb.soar_exact_mips(X, Qcal, w.k)[0]
-    Ztr = torch.cat([sb.soar_probe_features(ix, Qtr[i:i + batch], 64) for i in range(0, n_train, batch)])
+    Ztr = torch.cat([sb.soar_probe_features(ix, Qtr[i:i + batch], PROBE_TOP) for i in range(0, n_train, batch)])
     labels = torch.cat([sb.soar_probe_labels(ix, Qtr[i:i + batch], truth_tr[i:i + batch], RECALL_TARGET)
                         for i in range(0, n_train, batch)])
     del X
     params, losses = probe.train(ix, Ztr, labels, hidden=256, steps=3000, batch=4096, lr=1e-3, bf16=True)
-    t_cap = int(torch.quantile(labels.float()[:200_000], 0.99).item())
-    Zcal = sb.soar_probe_features(ix, Qcal, 64)
+    t_cap = min(PROBE_TOP, int(torch.quantile(labels.float()[:200_000], 0.99).item()))
+    Zcal = sb.soar_probe_features(ix, Qcal, PROBE_TOP)
     alpha = probe.calibrate_alpha(ix, params, 256, Zcal, Qcal, truth_cal, w.k, t_cap)
     train_s = time.perf_counter() - t1
 
     def step():
-        Z = sb.soar_probe_features(ix, Q, 64)
-        tq = sb.soar_mlp_predict_probes(params, Z.shape[1], 256, Z, alpha, t_cap, True)
-        return sb.soar_search(ix, Q, w.k, int(tq.max()), t_per_query=tq), tq
+        ids_, sc_, tq = sb.soar_search_learned(ix, Q, w.k, PROBE_TOP, params, 256, alpha, t_cap, True)
+        return (ids_, sc_), tq
 
     for _ in range(warmup):
         step()
@@ -759,7 +761,8 @@ def precision_at_size(sb, dev, steps, warmup, n_train=1_000_000, n_test=10_000, 
                "mean_t": float(tq.float().mean()), "max_t": int(tq.max()), "alpha": alpha, "t_cap": t_cap,
                "train_queries": n_train, "train_steps": 3000, "final_train_loss": losses[-1],
                "label_mean": float(labels.float().mean()), "label_ground_truth_s": label_gt_s,
-               "setup_s": train_s}
+               "setup_s": train_s,
+               "path": f"soar_search_learned: top-{PROBE_TOP} selection with scores, features, network, scan"}
     log(f"[bench] precision learned probe: {learned}")
     res = {"workload": f"precision: n={w.n} d={w.d} bf16 c={w.c} lambda={w.lam} spills={w.spills} nq={n_test} k={w.k}",
            "index": "bf16 rows scanned on the tensor cores (kind::f16), exact fp32 finishing",

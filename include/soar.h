@@ -403,6 +403,23 @@ SOAR_API soar_status soar_mlp_predict_probes(const float* params, int32_t d_in, 
                                              int32_t batch, int32_t bf16, float alpha, int32_t c, int32_t* t_out,
                                              cudaStream_t stream);
 
+/* soar_search with the learned probe count in one call: the search selects
+ * each query's top `top` partitions with their scores (the selection of
+ * soar_probe_features, done once), the network predicts the query's count
+ * clamp(ceil(alpha * exp(y)), 1, t_cap) from those features, and the query
+ * probes that many of its top partitions, best first.  The results equal
+ * soar_search(index, Q, ..., t = top, t_per_query = those counts).
+ *   params, hidden, bf16   the network (d_in = d + top), as soar_mlp_forward
+ *   t_out                  [nq] int32 device, the counts used (nullable)
+ *   rescore, ids_out, scores_out as soar_search.
+ * Requires 1 <= t_cap <= top <= min(c, 8192), alpha finite and > 0; the
+ * fastest path takes top <= 32 (the selection kernel of Section 2.2 keeps up
+ * to 32 partitions per query in registers). */
+SOAR_API soar_status soar_search_learned(const soar_index* index, const void* Q, soar_dtype dtype, int64_t nq,
+                                         int32_t k, int32_t top, const float* params, int32_t hidden, int32_t bf16,
+                                         float alpha, int32_t t_cap, int32_t rescore, int64_t* ids_out,
+                                         float* scores_out, int32_t* t_out, cudaStream_t stream);
+
 /* ------------------------------------------------------------------ *
  * Serving loop (an extension; the paper describes no serving system)
  * ------------------------------------------------------------------ *

@@ -88,6 +88,8 @@ _SIGS = {
     "soar_mlp_backward": ([_P, _I32, _I32, _P, _P, _I32, _I32, _P, _P, _P], _I32),
     "soar_mlp_adam": ([_P, _P, _P, _P, _I64, _I32, _F32, _F32, _F32, _F32, _P], _I32),
     "soar_mlp_predict_probes": ([_P, _I32, _I32, _P, _I32, _I32, _F32, _I32, _P, _P], _I32),
+    "soar_search_learned": ([_P, _P, _I32, _I64, _I32, _I32, _P, _I32, _I32, _F32, _I32, _I32, _P, _P, _P, _P],
+                            _I32),
     "soar_kernel_launches": ([], ct.c_uint64),
     "soar_set_wait_limit": ([_I64], _I32),
     "soar_stage_timing": ([_I32], _I32),
@@ -479,6 +481,20 @@ def soar_mlp_adam(params: torch.Tensor, grads: torch.Tensor, m1: torch.Tensor, m
     _check(load().soar_mlp_adam(_dev(params, "params", torch.float32, 1), _dev(grads, "grads", torch.float32, 1),
                                 _dev(m1, "m1", torch.float32, 1), _dev(m2, "m2", torch.float32, 1),
                                 params.numel(), step, lr, beta1, beta2, eps, _stream(stream)))
+
+
+def soar_search_learned(index: Index, Q: torch.Tensor, k: int, top: int, params: torch.Tensor, hidden: int,
+                        alpha: float, t_cap: int, bf16: bool = True, rescore: int = 0, stream=None):
+    """Search with the learned per-query probe count in one call; returns (ids, scores, counts)."""
+    nq = Q.shape[0]
+    ids = torch.empty((nq, k), dtype=torch.int64, device=Q.device)
+    scores = torch.empty((nq, k), dtype=torch.float32, device=Q.device)
+    t = torch.empty((nq,), dtype=torch.int32, device=Q.device)
+    _check(load().soar_search_learned(index.handle, _dev(Q, "Q", ndim=2), _dtype(Q), nq, k, top,
+                                      _dev(params, "params", torch.float32, 1), hidden, int(bf16), float(alpha),
+                                      t_cap, rescore, _dev(ids, "ids"), _dev(scores, "scores"), _dev(t, "t"),
+                                      _stream(stream)))
+    return ids, scores, t
 
 
 def soar_mlp_predict_probes(params: torch.Tensor, d_in: int, hidden: int, Z: torch.Tensor, alpha: float, c: int,

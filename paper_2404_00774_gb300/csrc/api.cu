@@ -518,6 +518,29 @@ soar_status soar_mlp_predict_probes(const float* params, int32_t d_in, int32_t h
   });
 }
 
+soar_status soar_search_learned(const soar_index* index, const void* Q, soar_dtype dtype, int64_t nq, int32_t k,
+                                int32_t top, const float* params, int32_t hidden, int32_t bf16, float alpha,
+                                int32_t t_cap, int32_t rescore, int64_t* ids_out, float* scores_out, int32_t* t_out,
+                                cudaStream_t stream) {
+  return guarded([&] {
+    SOAR_REQUIRE(index && Q && params && ids_out && scores_out, "null pointer");
+    SOAR_REQUIRE(valid_dtype(dtype), "unknown dtype");
+    SOAR_REQUIRE(nq >= 1 && nq * (int64_t)top < (int64_t(1) << 31) && nq < (int64_t(1) << 31),
+                 "nq * top must be in [1, 2^31)");
+    SOAR_REQUIRE(k >= 1 && k <= 1024, "k must be in [1, 1024]");
+    SOAR_REQUIRE(top >= 1 && top <= index->data.c && top <= 8192, "top must be in [1, min(c, 8192)]");
+    SOAR_REQUIRE(t_cap >= 1 && t_cap <= top, "t_cap must be in [1, top]");
+    SOAR_REQUIRE(hidden >= 1, "hidden must be >= 1");
+    SOAR_REQUIRE(std::isfinite(alpha) && alpha > 0.f, "alpha must be finite and > 0");
+    if (index->data.mode == SOAR_SCORE_FP8 || index->data.mode == SOAR_SCORE_PQ4)
+      SOAR_REQUIRE(rescore >= k && rescore <= 4096, "rescore must be in [k, 4096] for an FP8 or PQ4 index");
+    soar::Scratch scr(stream);
+    const soar::LearnedProbe lp{params, index->data.d + top, hidden, bf16 != 0, alpha, t_cap, t_out};
+    soar::search(index->data, Q, dtype, nq, k, top, nullptr, rescore, ids_out, scores_out, stream, scr, nullptr, 0,
+                 &lp);
+  });
+}
+
 soar_status soar_check_device(void) {
   return guarded([&] {
     SOAR_CUDA(cudaDeviceSynchronize());

@@ -153,6 +153,22 @@ void probe_features(const IndexData& ix, const void* Q, soar_dtype dt, int64_t n
                     cudaStream_t s, Scratch& scr);
 void probe_labels(const IndexData& ix, const void* Q, soar_dtype dt, int64_t nq, const int64_t* truth, int k,
                   float target, int32_t* labels, cudaStream_t s, Scratch& scr);
+// Z [nq][d + top] = [q || top_s] (the probe features, from scores already selected).
+void features_from_scores(const void* Q, soar_dtype dt, int64_t nq, int d, const float* top_s, int top, float* Z,
+                          cudaStream_t s);
+
+// The learned probe count inside a search: the search's own top-t selection
+// (with scores) gives the features, the network predicts each query's probe
+// count, clamp(ceil(alpha exp(y)), 1, t_cap), and the query probes that many
+// of its top-t partitions.  t_out (nullable) receives the counts.
+struct LearnedProbe {
+  const float* params;
+  int d_in, hidden;
+  bool bf16;
+  float alpha;
+  int t_cap;
+  int32_t* t_out;
+};
 
 // Same computation as select_partitions with all scratch carved from a
 // caller-provided device buffer of select_scratch_bytes(ix, nq) bytes.
@@ -162,9 +178,11 @@ void select_partitions_in(const IndexData& ix, const void* Q, soar_dtype dt, int
 
 // With `coarse` set, the probed partitions come from multilevel_select
 // (t1 coarse probes) instead of the flat top-t selection.
+// With `learned` set, the per-query probe counts come from the network.
 void search(const IndexData& ix, const void* Q, soar_dtype dt, int64_t nq, int32_t k, int32_t t,
             const int32_t* t_per_query, int32_t rescore, int64_t* ids_out, float* scores_out,
-            cudaStream_t s, Scratch& scr, const IndexData* coarse = nullptr, int32_t t1 = 0);
+            cudaStream_t s, Scratch& scr, const IndexData* coarse = nullptr, int32_t t1 = 0,
+            const LearnedProbe* learned = nullptr);
 
 // Two-level partition selection: an IVF search over the fine centroids (the
 // rows of `coarse`) with t1 coarse probes and k = t.  top [nq][t] fine

@@ -287,6 +287,16 @@ void probe_features(const IndexData& ix, const void* Q, soar_dtype dt, int64_t n
   SOAR_LAUNCHED();
 }
 
+void features_from_scores(const void* Q, soar_dtype dt, int64_t nq, int d, const float* top_s, int top, float* Z,
+                          cudaStream_t s) {
+  if (dt == SOAR_F32)
+    build_features<float><<<(unsigned)nq, 128, 0, s>>>(static_cast<const float*>(Q), nq, d, top_s, top, Z);
+  else
+    build_features<__nv_bfloat16><<<(unsigned)nq, 128, 0, s>>>(static_cast<const __nv_bfloat16*>(Q), nq, d, top_s,
+                                                               top, Z);
+  SOAR_LAUNCHED();
+}
+
 void probe_labels(const IndexData& ix, const void* Q, soar_dtype dt, int64_t nq, const int64_t* truth, int k,
                   float target, int32_t* labels, cudaStream_t s, Scratch& scr) {
   // every centroid score of every query, computed exactly as the search ranks them

@@ -1024,9 +1024,23 @@ void multilevel_select(const IndexData& coarse, const void* Q, soar_dtype dt, in
   SOAR_LAUNCHED();
 }
 
+// The search's selection with the learned probe count: the top t with their
+// scores, the features [q || scores], the network's per-query counts.
+static const int32_t* learned_select(const IndexData& ix, const void* Q, soar_dtype dt, const float* Qf,
+                                     const float* qscale, int64_t nq, int qstride, int t, const LearnedProbe& lp,
+                                     int32_t* top, cudaStream_t s, Scratch& scr) {
+  float* top_s = scr.get<float>((size_t)nq * t);
+  select_prepared(ix, Qf, qscale, nq, qstride, t, top, top_s, s, scr);
+  float* Z = scr.get<float>((size_t)nq * (ix.d + t));
+  features_from_scores(Q, dt, nq, ix.d, top_s, t, Z, s);
+  int32_t* tq = lp.t_out ? lp.t_out : scr.get<int32_t>(nq);
+  mlp_predict(lp.params, lp.d_in, lp.hidden, Z, (int)nq, lp.bf16, lp.alpha, lp.t_cap, nullptr, tq, s, scr);
+  return tq;
+}
+
 void search(const IndexData& ix, const void* Q, soar_dtype dt, int64_t nq, int32_t k, int32_t t,
             const int32_t* tpq, int32_t rescore, int64_t* ids_out, float* scores_out, cudaStream_t s,
-            Scratch& scr, const IndexData* coarse, int32_t t1) {
+            Scratch& scr, const IndexData* coarse, int32_t t1, const LearnedProbe* learned) {
   const bool fp8 = ix.mode == SOAR_SCORE_FP8;
   if (!fp8 && ix.tc_rows && k <= scan_tc_max_k(ix)) {
     // fp32 index: tensor-core screening with exact fp32 rescoring
@@ -1040,6 +1054,8 @@ void search(const IndexData& ix, const void* Q, soar_dtype dt, int64_t nq, int32
       int32_t* found = scr.get<int32_t>(nq);
       multilevel_select(*coarse, Q, dt, nq, t, t1, top, nullptr, found, s, scr);
       tpq = found;
+    } else if (learned) {
+      tpq = learned_select(ix, Q, dt, Qf, nullptr, nq, qstride, t, *learned, top, s, scr);
     } else {
       select_prepared(ix, Qf, nullptr, nq, qstride, t, top, nullptr, s, scr);
     }
@@ -1093,6 +1109,8 @@ void search(const IndexData& ix, const void* Q, soar_dtype dt, int64_t nq, int32
     int32_t* found = scr.get<int32_t>(nq);
     multilevel_select(*coarse, Q, dt, nq, t, t1, top, nullptr, found, s, scr);
     tpq = found;
+  } else if (learned) {
+    tpq = learned_select(ix, Q, dt, Qf, qscale, nq, qstride, t, *learned, top, s, scr);
   } else {
     select_prepared(ix, Qf, qscale, nq, qstride, t, top, nullptr, s, scr);
   }

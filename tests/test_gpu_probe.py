@@ -11,6 +11,7 @@ import torch
 import oracle
 import synth
 from oracle import probe_mlp
+from parity_util import topk_mismatches
 
 pytestmark = pytest.mark.gpu
 
@@ -149,3 +150,28 @@ def test_learned_probe_count_saves_probes_at_recall_target(soar):
     assert rec_mlp >= 0.88
     assert mean_t < fixed
     ix.close()
+
+
+def test_search_learned_equals_features_predict_search_and_oracle(soar, tiny_index):
+    # the one-call learned-probe search against the three calls it fuses
+    # (features, prediction, search with those counts) and against the
+    # oracle's IVF search with the same per-query counts
+    X, Q, C, A, ix = tiny_index
+    d, top, hidden, cap = X.shape[1], 32, 64, 16
+    params = _t(_random_params(d + top, hidden, 51)[0])
+    Qd = _t(Q)
+    Z = soar.soar_probe_features(ix, Qd, top)
+    y = soar.soar_mlp_forward(params, d + top, hidden, Z, bf16=True)
+    alpha = float(6.0 / torch.exp(y.median()))     # counts spread around 6
+    t_ref = soar.soar_mlp_predict_probes(params, d + top, hidden, Z, alpha, cap, True)
+    ids, scores, t = soar.soar_search_learned(ix, Qd, 10, top, params, hidden, alpha, cap, bf16=True)
+    np.testing.assert_array_equal(t.cpu().numpy(), t_ref.cpu().numpy())
+    tn = t.cpu().numpy()
+    assert tn.min() >= 1 and tn.max() <= cap and len(np.unique(tn)) > 2
+    want_i, want_s = soar.soar_search(ix, Qd, 10, top, t_per_query=t)
+    np.testing.assert_array_equal(ids.cpu().numpy(), want_i.cpu().numpy())
+    np.testing.assert_array_equal(scores.cpu().numpy(), want_s.cpu().numpy())
+    off, ivf = oracle.build_ivf(A, C.shape[0])
+    wi, ws = oracle.ivf_search(Q, X, C, off, ivf, 10, top, t_per_query=tn)
+    Xd, Qf = X.astype(np.float64), Q.astype(np.float64)
+    assert topk_mismatches(ids.cpu().numpy(), wi, ws, lambda q, i: Xd[np.asarray(i, np.int64)] @ Qf[q]) == []
