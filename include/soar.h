@@ -76,7 +76,10 @@ typedef enum { SOAR_F32 = 0, SOAR_BF16 = 1 } soar_dtype;
  *   and rescore the best `rescore` candidates exactly.  Built with
  *   soar_index_build_pq.
  */
-typedef enum { SOAR_SCORE_F32 = 0, SOAR_SCORE_BF16 = 1, SOAR_SCORE_FP8 = 2, SOAR_SCORE_PQ4 = 3 } soar_score_mode;
+/* (Value 1 is unused: bf16 storage comes from the input dtype.  An index
+ * built from SOAR_BF16 data with SOAR_SCORE_F32 keeps the bf16 rows, screens
+ * them on the tensor cores and scores them exactly.) */
+typedef enum { SOAR_SCORE_F32 = 0, SOAR_SCORE_FP8 = 2, SOAR_SCORE_PQ4 = 3 } soar_score_mode;
 
 typedef struct soar_index soar_index;   /* opaque; owns its device memory */
 

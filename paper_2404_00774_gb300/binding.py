@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libsoar.so")
 
 SOAR_OK, SOAR_EINVAL, SOAR_ENOMEM, SOAR_ECUDA, SOAR_ETIMEOUT, SOAR_EUNSUPPORTED = range(6)
 SOAR_F32, SOAR_BF16 = 0, 1
-SOAR_SCORE_F32, SOAR_SCORE_BF16, SOAR_SCORE_FP8, SOAR_SCORE_PQ4 = 0, 1, 2, 3
+SOAR_SCORE_F32, SOAR_SCORE_FP8, SOAR_SCORE_PQ4 = 0, 2, 3
 STATUS_NAMES = {0: "SOAR_OK", 1: "SOAR_EINVAL", 2: "SOAR_ENOMEM", 3: "SOAR_ECUDA",
                 4: "SOAR_ETIMEOUT", 5: "SOAR_EUNSUPPORTED"}
 

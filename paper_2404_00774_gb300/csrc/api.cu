@@ -186,10 +186,8 @@ soar_status soar_index_build(const void* X, soar_dtype dtype, int64_t n, int32_t
     SOAR_REQUIRE(n >= 1 && d >= 1 && d <= 4096 && c >= 1, "bad sizes");
     SOAR_REQUIRE(spills >= 0 && spills <= 4 && c >= 1 + spills, "spills must be in [0, 4] and <= c - 1");
     SOAR_REQUIRE(n * (1 + spills) < (int64_t(1) << 31), "n * (1 + spills) must be < 2^31");
-    SOAR_REQUIRE(mode == SOAR_SCORE_F32 || mode == SOAR_SCORE_FP8 || mode == SOAR_SCORE_BF16 ||
-                     mode == SOAR_SCORE_PQ4, "unknown mode");
+    SOAR_REQUIRE(mode == SOAR_SCORE_F32 || mode == SOAR_SCORE_FP8 || mode == SOAR_SCORE_PQ4, "unknown mode");
     SOAR_REQUIRE(mode != SOAR_SCORE_PQ4, "a SOAR_SCORE_PQ4 index needs its codebooks: use soar_index_build_pq");
-    if (mode == SOAR_SCORE_BF16) soar::fail(SOAR_EUNSUPPORTED, "soar_index_build: SOAR_SCORE_BF16 not implemented");
     soar_index* ix = new soar_index;
     ix->data.n = n;
     ix->data.d = d;

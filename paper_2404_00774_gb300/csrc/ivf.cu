@@ -310,7 +310,7 @@ void build_index(IndexData& ix, const void* X, soar_dtype dt, const float* C, co
     SOAR_LAUNCHED();
     pq_encode_index(ix, X, dt, s, scr);
   } else {
-    fail(SOAR_EUNSUPPORTED, "soar_index_build: SOAR_SCORE_BF16 is not implemented");
+    fail(SOAR_EINVAL, "soar_index_build: unknown score mode");
   }
 
   // one synchronisation: validity flag and the largest partition
