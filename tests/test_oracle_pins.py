@@ -754,3 +754,84 @@ def test_pq_search_rescoring_everything_is_brute_force():
     wi, ws = oracle.mips_topk(Q, X, 10)
     np.testing.assert_array_equal(gi, wi)
     np.testing.assert_allclose(gs, ws, rtol=1e-12)
+
+
+# ------------------------------- FP8 selection, probe positions, MLP forward
+
+def test_select_partitions_fp8_on_exact_rows_is_the_exact_selection():
+    # every query and centroid exactly representable in its scaled FP8 form,
+    # the centroid scales spread over 2^-4..1: the FP8 selection must equal
+    # the fp64 one id for id and score for score (a score without the
+    # per-centroid scale would rank the centroids differently)
+    rng = np.random.default_rng(43)
+    Q = _fp8_exact_rows(rng, 25, 10, 2)
+    C = _fp8_exact_rows(rng, 40, 10, 4)
+    for t in (1, 6, 40):
+        got_i, got_s = oracle.select_partitions_fp8(Q, C, t)
+        want_i, want_s = oracle.select_partitions(Q, C, t)
+        np.testing.assert_array_equal(got_i, want_i)
+        np.testing.assert_array_equal(got_s, want_s)
+    c8, _ = oracle.quantize_rows_fp8(C)
+    q8, _ = oracle.quantize_rows_fp8(Q)
+    unscaled = q8.astype(np.float64) @ c8.astype(np.float64).T
+    exact = Q.astype(np.float64) @ C.astype(np.float64).T
+    assert not np.array_equal(np.argsort(-unscaled, axis=1, kind="stable")[:, :6],
+                              np.argsort(-exact, axis=1, kind="stable")[:, :6])
+
+
+def test_select_partitions_fp8_rounding_by_hand():
+    # every row's largest entry is 1.75, so its scale 1.75 / 448 = 2^-8 is
+    # exact in fp32.  q = (1.75, 0) encodes exactly (code 448).  Centroid 0 =
+    # (0.97 * 1.75, 1.75): 0.97 * 448 = 434.56 lies above the midpoint 432 of
+    # the E4M3 neighbours 416 and 448, so its first code is 448 and its FP8
+    # score 448 * 448 * 2^-16 = 3.0625 ties with centroid 1 = (1.75, 0)
+    # (exact score 3.0625); the tie goes to the lower id, so FP8 ranks 0
+    # first where the exact scores (2.97 against 3.06) rank 1 first
+    Q = np.array([[1.75, 0.0]], dtype=np.float32)
+    C = np.array([[0.97 * 1.75, 1.75], [1.75, 0.0]], dtype=np.float32)
+    ids, sc = oracle.select_partitions_fp8(Q, C, 2)
+    assert ids.tolist() == [[0, 1]]
+    np.testing.assert_array_equal(sc, [[3.0625, 3.0625]])
+    assert oracle.select_partitions(Q, C, 2)[0].tolist() == [[1, 0]]
+
+
+def test_partition_positions_by_hand_with_ties():
+    # scores of query 0: (0.5, 1, 0.5, -1) -> probe order 1, 0, 2, 3 (the tie
+    # of partitions 0 and 2 goes to the lower id); query 1 scores (0, 0, 2, 1)
+    # -> order 2, 3, 0, 1
+    Q = np.array([[1.0, 0.0], [0.0, 1.0]])
+    C = np.array([[0.5, 0.0], [1.0, 0.0], [0.5, 2.0], [-1.0, 1.0]])
+    pos = oracle.partition_positions(Q, C)
+    assert pos.tolist() == [[2, 1, 3, 4], [3, 4, 1, 2]]
+
+
+def test_partition_positions_without_ties_are_ranks():
+    # without ties the position of partition p is 1 + the number of
+    # centroids that score strictly higher (Rank(q, C_p, C) of Section 2.1),
+    # and reading the positions back gives the full probe order
+    rng = np.random.default_rng(44)
+    Q, C = rng.standard_normal((7, 5)), rng.standard_normal((30, 5))
+    pos = oracle.partition_positions(Q, C)
+    S = Q @ C.T
+    for i in range(7):
+        for p in range(30):
+            assert pos[i, p] == 1 + sum(1 for j in range(30) if S[i, j] > S[i, p])
+    order, _ = oracle.select_partitions(Q, C, 30)
+    for i in range(7):
+        assert [int(np.nonzero(pos[i] == r)[0][0]) for r in range(1, 31)] == order[i].tolist()
+
+
+def test_mlp_forward_by_hand():
+    # W1 [H, D_in] row-major, ReLU after both hidden layers, none after the
+    # output: row 0 = (3, 1): a1 = (2, 5), h1 = (2, 5), a2 = (7.5, -2),
+    # h2 = (7.5, 0), y = 15 + 0.25; row 1 = (-1, 2): a1 = (-3, -3), h1 = 0,
+    # a2 = (0.5, 0), y = 1 + 0.25
+    p = {"W1": np.array([[1.0, -1.0], [2.0, 0.0]]), "b1": np.array([0.0, -1.0]),
+         "W2": np.array([[1.0, 1.0], [-1.0, 0.0]]), "b2": np.array([0.5, 0.0]),
+         "W3": np.array([[2.0, -3.0]]), "b3": np.array([0.25])}
+    y, (Z, a1, h1, a2, h2) = probe_mlp.forward(p, np.array([[3.0, 1.0], [-1.0, 2.0]]))
+    np.testing.assert_array_equal(y, [15.25, 1.25])
+    np.testing.assert_array_equal(a1, [[2.0, 5.0], [-3.0, -3.0]])
+    np.testing.assert_array_equal(h2, [[7.5, 0.0], [0.5, 0.0]])
+    assert probe_mlp.loss(p, np.array([[3.0, 1.0], [-1.0, 2.0]]), np.array([15.0, 2.25])) == pytest.approx(
+        (0.25 ** 2 + 1.0) / 2)
