@@ -205,6 +205,8 @@ def test_primary_assign_matches_cdist_and_ties():
     assert np.all(pi[:5] == 3)                   # tie goes to the lower index
     assert np.all(gap[:5] == 0)
     np.testing.assert_allclose(best, D.min(axis=1), atol=1e-10)
+    Ds = np.sort(D, axis=1)                      # gap: runner-up minus best
+    np.testing.assert_allclose(gap, Ds[:, 1] - Ds[:, 0], atol=1e-10)
 
 
 def test_mips_topk_matches_pure_python_with_ties():
@@ -835,3 +837,118 @@ def test_mlp_forward_by_hand():
     np.testing.assert_array_equal(h2, [[7.5, 0.0], [0.5, 0.0]])
     assert probe_mlp.loss(p, np.array([[3.0, 1.0], [-1.0, 2.0]]), np.array([15.0, 2.25])) == pytest.approx(
         (0.25 ** 2 + 1.0) / 2)
+
+
+# ------------------------------ ties, gaps and edge values (mutation checks)
+
+def test_soar_assign_ties_and_gaps_by_loops():
+    # integer points and centroids, two centroids duplicated: squared
+    # distances are exact, a duplicate's loss equals its twin's bit for bit,
+    # so ties are exact and must go to the lower index, for the primary and
+    # for every spill; each decision's gap (runner-up minus best among the
+    # centroids still allowed) and best loss match loops over the direct form
+    rng = np.random.default_rng(45)
+    n, c, d = 80, 10, 4
+    X = rng.integers(-3, 4, size=(n, d)).astype(np.float64)
+    C = rng.integers(-3, 4, size=(c, d)).astype(np.float64)
+    C[6], C[8] = C[2], C[4]
+    X[:10] = C[2]                                     # zero residuals on a duplicated centroid
+    for lam in (0.0, 1.5):
+        got, gaps, best = oracle.soar_assign(X, C, lam, 2, return_gaps=True)
+        for i in range(n):
+            x = X[i]
+            a, dirs = [], []
+            for j in range(3):
+                def L(m):
+                    rp = x - C[m]
+                    return float(rp @ rp) + lam * sum(float(rp @ u) ** 2 for u in dirs)
+                losses = sorted((L(m), m) for m in range(c) if m not in a)
+                a.append(losses[0][1])
+                assert got[i, j] == losses[0][1], (lam, i, j)
+                assert best[i, j] == pytest.approx(losses[0][0], rel=1e-9, abs=1e-9)
+                assert gaps[i, j] == pytest.approx(losses[1][0] - losses[0][0], rel=1e-9, abs=1e-9)
+                r = x - C[a[-1]]
+                nr = math.sqrt(float(r @ r))
+                dirs.append(r / nr if nr > 0 else np.zeros(d))
+        assert np.all(got[:10, 0] == 2) and np.all(got[:10, 1] == 6)   # the exact twin, lower index first
+
+
+@pytest.mark.parametrize("target", [0.75, 0.85])
+def test_probe_labels_with_a_fractional_rank_equal_direct_sweep(target):
+    # target * k = 7.5 and 8.5: the label needs ceil(target * k) neighbours
+    X, Q, C, A, off, ids = _small_index()
+    truth, _ = oracle.mips_topk(Q, X, 10)
+    lab = oracle.probe_labels(Q, C, A, truth, target)
+    rec = np.stack([oracle.recall_at_k(oracle.ivf_search(Q, X, C, off, ids, 10, t)[0], truth)
+                    for t in range(1, C.shape[0] + 1)])
+    for i in range(Q.shape[0]):
+        assert lab[i] == 1 + int(np.argmax(rec[:, i] >= target - 1e-12))
+
+
+def test_bf16_round_ties_to_even():
+    torch = pytest.importorskip("torch")
+    # 1 + 2^-8 lies halfway between 1 and 1 + 2^-7: even mantissa -> 1;
+    # 1 + 3 * 2^-8 lies halfway between 1 + 2^-7 (odd) and 1 + 2^-6 (even)
+    v = np.array([1 + 2 ** -8, 1 + 3 * 2 ** -8, -(1 + 2 ** -8), -(1 + 3 * 2 ** -8)], dtype=np.float32)
+    np.testing.assert_array_equal(oracle.bf16_round(v), [1.0, 1 + 2 ** -6, -1.0, -(1 + 2 ** -6)])
+    # every exact tie pattern (low 16 bits 0x8000) against torch's conversion
+    rng = np.random.default_rng(46)
+    bits = (rng.integers(0x0080, 0x7F00, size=4000, dtype=np.uint32) << 16) | 0x8000
+    bits[::2] |= 0x80000000
+    t = bits.view(np.float32)
+    want = torch.from_numpy(t.copy()).to(torch.bfloat16).to(torch.float32).numpy()
+    np.testing.assert_array_equal(oracle.bf16_round(t), want)
+
+
+def test_precision_search_probes_the_fp8_selection():
+    # the centroids of the FP8 hand case: with t = 1 the FP8 scores probe
+    # partition 0, the exact scores would probe partition 1; each partition
+    # holds one point, so the answer shows which partition was probed
+    Q = np.array([[1.75, 0.0]], dtype=np.float32)
+    C = np.array([[0.97 * 1.75, 1.75], [1.75, 0.0]], dtype=np.float32)
+    X = np.array([[0.0, 1.0], [1.0, 0.0]], dtype=np.float32)
+    off, ids = oracle.build_ivf(np.array([[0], [1]]), 2)
+    got_i, got_s = oracle.precision_search(Q, X, C, off, ids, 1, 1, 1)
+    assert got_i.tolist() == [[0]] and got_s.tolist() == [[0.0]]
+    assert oracle.ivf_search(Q, X, C, off, ids, 1, 1)[0].tolist() == [[1]]
+
+
+def test_mlp_adam_first_step_with_small_and_non_unit_gradients():
+    # first step: m = 0.1 g, v = 0.001 g^2, bias-corrected m = g and v = g^2,
+    # update = lr * g / (|g| + eps): for g = 0.5 that is lr * 0.5 / (0.5 + 1e-8),
+    # for g = 1e-6 it is lr / 1.01 (eps added to the root, not under it)
+    names = probe_mlp.PARAM_NAMES
+    p = {k: np.zeros((1, 1)) if k.startswith("W") else np.zeros(1) for k in names}
+    m = {k: np.zeros_like(x) for k, x in p.items()}
+    v = {k: np.zeros_like(x) for k, x in p.items()}
+    gv = {"W1": 0.5, "b1": 1e-6, "W2": -3.0, "b2": 0.0, "W3": 1.0, "b3": -1e-6}
+    g = {k: np.full_like(p[k], gv[k]) for k in names}
+    probe_mlp.adam_step(p, g, m, v, 1, 0.1)
+    assert p["W1"][0, 0] == pytest.approx(-0.1 * 0.5 / (0.5 + 1e-8), rel=1e-12)
+    assert p["b1"][0] == pytest.approx(-0.1 * 1e-6 / (1e-6 + 1e-8), rel=1e-12)
+    assert p["W2"][0, 0] == pytest.approx(0.1 * 3.0 / (3.0 + 1e-8), rel=1e-12)
+    assert p["b2"][0] == 0.0
+    assert p["b3"][0] == pytest.approx(0.1 / 1.01, rel=1e-12)
+    assert v["W2"][0, 0] == pytest.approx(0.001 * 9.0, rel=1e-12)
+
+
+def test_predict_probes_clamps_an_underflowed_count_to_one():
+    H = 2
+    p = {"W1": np.zeros((H, 2)), "b1": np.zeros(H), "W2": np.zeros((H, H)), "b2": np.zeros(H),
+         "W3": np.zeros((1, H)), "b3": np.array([-1000.0])}    # exp(y) underflows to 0
+    assert probe_mlp.predict_probes(p, np.zeros((3, 2)), 1.0, 50).tolist() == [1, 1, 1]
+
+
+def test_init_params_he_uniform_bounds():
+    # He-uniform: U(-sqrt(6 / fan_in), sqrt(6 / fan_in)) per weight matrix,
+    # zero biases; with 1 600 draws the extremes come close to the bound
+    d_in, hidden = 4, 400
+    p = probe_mlp.init_params(d_in, hidden, 7)
+    for name, fan_in, shape in (("W1", d_in, (hidden, d_in)), ("W2", hidden, (hidden, hidden)),
+                                ("W3", hidden, (1, hidden))):
+        lim = math.sqrt(6.0 / fan_in)
+        assert p[name].shape == shape
+        assert np.abs(p[name]).max() <= lim
+        assert np.abs(p[name]).max() >= 0.95 * lim
+    for name in ("b1", "b2", "b3"):
+        assert not np.any(p[name])
