@@ -952,3 +952,15 @@ def test_init_params_he_uniform_bounds():
         assert np.abs(p[name]).max() >= 0.95 * lim
     for name in ("b1", "b2", "b3"):
         assert not np.any(p[name])
+
+
+def test_kmeans_update_sums_in_fp64():
+    # one Lloyd step with one cluster: the new centroid is the mean of the
+    # 20 000 fp32 points summed in fp64 (exactly: math.fsum) and rounded to
+    # fp32; an fp32 running sum of values near 1 000 drifts by about 0.1
+    rng = np.random.default_rng(47)
+    n = 20_000
+    X = (1000.0 + rng.random((n, 2))).astype(np.float32)
+    C = oracle.kmeans(X, np.array([0]), 1)
+    want = np.array([math.fsum(X[:, j].astype(np.float64)) / n for j in range(2)]).astype(np.float32)
+    np.testing.assert_array_equal(C[0], want)
