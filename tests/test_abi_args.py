@@ -231,3 +231,94 @@ def test_mlp_param_count_follows_the_network_layout(lib):
         assert lib.soar_mlp_param_count(d_in, hidden) == want
     assert lib.soar_mlp_param_count(0, 16) == -1
     assert lib.soar_mlp_param_count(16, 0) == -1
+
+
+# ------------------------------------------ the Python binding against the header
+
+def test_binding_signatures_equal_the_header():
+    # every argument the binding marshals has the width the header declares
+    # (a 32-bit int where the C side reads 64 bits would shift every later
+    # argument), and every declared function has a binding signature
+    from paper_2404_00774_gb300 import binding
+    assert set(binding._SIGS) == set(DECLS)
+    for name, (args, res) in binding._SIGS.items():
+        ret, params = DECLS[name]
+        assert res == _RETURNS[ret], (name, res, ret)
+        assert len(args) == len(params), name
+        for a, (ptype, pname) in zip(args, params):
+            if "*" in ptype:
+                ok = a in (ct.c_void_p, ct.c_char_p) or issubclass(a, ct._Pointer)
+            else:
+                ok = a == _SCALARS[ptype.replace("const", "").strip()]
+            assert ok, (name, pname, ptype, a)
+
+
+def _header_structs():
+    """{typedef name: [(C type, field name)]} of the header's plain structs."""
+    src = ""
+    for f in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if f.endswith(".h"):
+            src += open(os.path.join(ROOT, "include", f)).read()
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    out = {}
+    for body, name in re.findall(r"typedef\s+struct\s*\{(.*?)\}\s*(\w+)\s*;", src, flags=re.S):
+        fields = []
+        for decl in body.split(";"):
+            decl = " ".join(decl.split())
+            if not decl:
+                continue
+            first, *rest = decl.split(",")
+            m = re.match(r"^(.*?)(\w+)\s*$", first)   # the last identifier is the first name
+            ctype = m.group(1).strip()
+            fields.append((ctype, m.group(2)))
+            base = ctype.rstrip("* ")
+            for nm in rest:                           # further names share the base type
+                fields.append((base + "*" * nm.count("*"), nm.strip("* ")))
+        out[name] = fields
+    return out
+
+
+_STRUCTS = {"soar_index_info": "IndexInfo", "soar_server_config": "ServerConfig",
+            "soar_server_metrics": "ServerStats"}
+
+
+def test_binding_structs_have_the_c_layout(tmp_path):
+    # a C program built from the header prints each struct's size and every
+    # field's offset and size; the ctypes structures must agree field by field
+    import shutil
+    import subprocess
+    from paper_2404_00774_gb300 import binding
+    gcc = shutil.which("gcc")
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    cuda_inc = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "include")
+    if not gcc or not os.path.exists(os.path.join(cuda_inc, "cuda_runtime_api.h")):
+        pytest.skip("gcc or the CUDA headers are missing")
+    structs = _header_structs()
+    assert set(_STRUCTS) <= set(structs)
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "soar.h"', "int main(void) {"]
+    for cname in _STRUCTS:
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for _, field in structs[cname]:
+            lines.append(f'  printf("{cname} {field} %zu %zu\\n", offsetof({cname}, {field}), '
+                         f'sizeof((({cname}*)0)->{field}));')
+    lines += ["  return 0;", "}"]
+    (tmp_path / "layout.c").write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-std=c11", "-I", os.path.join(ROOT, "include"), "-I", cuda_inc,
+                    str(tmp_path / "layout.c"), "-o", str(exe)], check=True, capture_output=True)
+    got = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    c_layout = {}
+    for ln in got:
+        parts = ln.split()
+        if len(parts) == 3:
+            c_layout[(parts[0], "")] = (int(parts[2]),)
+        elif len(parts) == 4:
+            c_layout[(parts[0], parts[1])] = (int(parts[2]), int(parts[3]))
+    for cname, pyname in _STRUCTS.items():
+        cls = getattr(binding, pyname)
+        assert [f for f, _ in cls._fields_] == [f for _, f in structs[cname]], cname
+        assert ct.sizeof(cls) == c_layout[(cname, "")][0], cname
+        for field, ftype in cls._fields_:
+            off, size = c_layout[(cname, field)]
+            assert getattr(cls, field).offset == off, (cname, field)
+            assert ct.sizeof(ftype) == size, (cname, field)
