@@ -149,10 +149,12 @@ def init_indices(n: int, c: int, seed: int) -> np.ndarray:
 
 
 def workload_arrays(name: str, n: int | None = None, nq: int | None = None):
-    """(X, Q, init_idx) for a named workload, optionally truncated in n / nq.
+    """(X, Q, init_idx) for a named workload, optionally with fewer points
+    (n) or queries (nq).
 
-    Truncation keeps the first rows of the same seeded stream, so a smaller
-    case is a prefix of the full one.
+    A smaller count draws from the same seeded stream in the same 2^18-row
+    chunks, so it is a prefix of the full draw only when it is a multiple of
+    the chunk; otherwise it is another draw from the same mixture.
     """
     w = WORKLOADS[name]
     n = w.n if n is None else n
