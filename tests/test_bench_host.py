@@ -140,3 +140,15 @@ def test_reference_arm_other_ranks_exit_without_work():
     r = _run_reference({"RANK": "1"})
     assert r.returncode == 0
     assert not [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+
+
+def test_time_oracle_reports_rate_wall_time_and_cpu_use():
+    import synth
+    w = synth.WORKLOADS["tiny"]
+    X, Q, _ = synth.workload_arrays("tiny", n=4000, nq=40)
+    C, off, ids = bench.oracle_index(X, w, w.lam, w.spills, train_rows=4000, iters=2)
+    qps, secs, busy = bench.time_oracle(X, Q, C, off, ids, w.k, 4, 24)
+    assert secs > 0 and qps == pytest.approx(24 / secs)
+    assert busy > 0
+    qps_all, _, _ = bench.time_oracle(X, Q, C, off, ids, w.k, 4, 10_000)   # more than there are
+    assert qps_all > 0
