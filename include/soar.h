@@ -170,15 +170,17 @@ SOAR_API soar_status soar_index_free(soar_index* index);
  * Index persistence, so that a large index (the inverted lists of Section 2.2
  * with the spilled copies of Section 3.5) is built once and reused.
  * soar_index_save writes every device array of the index, after a fixed
- * header (magic "SOARIDX1", format version 1, the scalar fields, the byte
+ * header (magic "SOARIDX1", format version 2, the scalar fields, the byte
  * size of each array), to the file `path` (host string; an existing file is
  * replaced).  soar_index_load reads such a file into a new index on the
  * current device; its searches return what the saved index returned, bit
  * for bit.  Both move the data through a pinned host buffer of 64 MiB with
  * one copy per chunk on `stream`, and synchronise `stream`; both return after
- * the file is complete.  A file that is not a SOAR index, has another format
- * version, a section of the wrong size or trailing bytes gives SOAR_EINVAL
- * (SOAR_EUNSUPPORTED for a newer version), with nothing allocated.
+ * the file is complete.  A file that is not a SOAR index, has header fields
+ * out of range, a section of the wrong size, a required section missing, or
+ * is shorter or longer than its header says gives SOAR_EINVAL; another format
+ * version gives SOAR_EUNSUPPORTED.  All of these are found on the host,
+ * before any device memory is taken.
  */
 SOAR_API soar_status soar_index_save(const soar_index* index, const char* path, cudaStream_t stream);
 SOAR_API soar_status soar_index_load(const char* path, soar_index** out /* host */, cudaStream_t stream);

@@ -10,6 +10,8 @@
 // An absent array (for example the FP8 scales of an fp32 index) has size 0.
 // Arrays move through a pinned host buffer in chunks of kChunk bytes with one
 // cudaMemcpyAsync per chunk on the caller's stream.
+#include <sys/stat.h>
+
 #include <cstdio>
 #include <cstring>
 #include <memory>
@@ -143,6 +145,14 @@ void load_index(IndexData& ix, const char* path, cudaStream_t s) {
     if (h.section_bytes[i] == 0 && (i == 0 || i == 1 || i == 2 || i == 5 || (i == 16 && h.mode == SOAR_SCORE_PQ4)))
       fail(SOAR_EINVAL, "soar_index_load: a required section is missing");
   }
+  // the file holds exactly the header and the sections it lists, checked on
+  // the host before any device memory is taken (the reads below check again)
+  uint64_t want = sizeof(FileHeader);
+  for (int i = 0; i < kSections; ++i) want += h.section_bytes[i];
+  struct stat st;
+  if (stat(path, &st) != 0) fail(SOAR_EINVAL, std::string("soar_index_load: cannot stat ") + path);
+  if ((uint64_t)st.st_size < want) fail(SOAR_EINVAL, "soar_index_load: file is truncated");
+  if ((uint64_t)st.st_size > want) fail(SOAR_EINVAL, "soar_index_load: trailing bytes after the last section");
   for (int i = 0; i < kSections; ++i) {
     if (h.section_bytes[i] == 0) continue;
     SOAR_CUDA(cudaMalloc(sec[i].ptr, sec[i].bytes));

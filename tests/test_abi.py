@@ -2,6 +2,7 @@
 that include/soar.h declares; host-side argument checks reject bad input
 before any device work (no compute calls here)."""
 import ctypes as ct
+import struct
 import os
 import re
 
@@ -92,3 +93,63 @@ def test_index_load_rejects_a_foreign_file_before_any_device_work(lib, tmp_path)
     assert b"not a SOAR index" in lib.soar_last_error()
     assert lib.soar_index_load(str(tmp_path / "missing.bin").encode(), ct.byref(out), None) == 1
     assert out.value is None
+
+
+# ---------------------------------------------- index files checked on the host
+
+_HDR = struct.Struct("<8sII5q12i17Q")      # magic, version, header bytes, 5 int64, 12 int32, 17 section sizes
+
+
+def _index_file(path, *, version=2, rows=None, sections=None, extra=b"", cut=0):
+    """A file shaped like a saved fp32 index of n = 10 points (d = 4, c = 2,
+    one spill) holding only the required sections: offsets, ids, vectors,
+    centroids, sized as the format defines them."""
+    n, d, c, spills = 10, 4, 2, 1
+    rows = n * (1 + spills) if rows is None else rows
+    sizes = [0] * 17
+    sizes[0] = 8 * (c + 1)            # offsets int64 [c + 1]
+    sizes[1] = 4 * rows               # ids int32 [rows]
+    sizes[2] = 4 * rows * d           # vectors fp32 [rows][row_stride = d]
+    sizes[5] = 4 * c * d              # centroids fp32 [c][d]
+    for i, b in (sections or {}).items():
+        sizes[i] = b
+    hdr = _HDR.pack(b"SOARIDX1", version, _HDR.size, n, rows, 12, 0, 0,
+                    d, c, spills, 0, 0, d, 0, 8, 8, 1, 0, 0, *sizes)
+    body = bytes(sum(sizes))
+    data = hdr + body + extra
+    path.write_bytes(data[:len(data) - cut])
+    return path
+
+
+def _load(lib, path):
+    lib.soar_index_load.argtypes = [ct.c_char_p, ct.POINTER(ct.c_void_p), ct.c_void_p]
+    lib.soar_index_load.restype = ct.c_int
+    lib.soar_last_error.restype = ct.c_char_p
+    lib.soar_index_free.argtypes = [ct.c_void_p]
+    out = ct.c_void_p()
+    st = lib.soar_index_load(str(path).encode(), ct.byref(out), None)
+    if st == 0:                       # only where a GPU took the arrays
+        lib.soar_index_free(out)
+    else:
+        assert out.value is None
+    return st, lib.soar_last_error()
+
+
+def test_index_file_checks_run_on_the_host(lib, tmp_path):
+    assert _HDR.size == 240
+    # an exact file passes every host check: with no GPU the first device
+    # allocation is what fails
+    st, msg = _load(lib, _index_file(tmp_path / "ok.bin"))
+    assert st != 1, msg
+    for kwargs, code, text in [
+        (dict(cut=1), 1, b"truncated"),
+        (dict(cut=200), 1, b"truncated"),
+        (dict(extra=b"\0"), 1, b"trailing bytes"),
+        (dict(sections={1: 76}), 1, b"section 1 has the wrong size"),
+        (dict(sections={5: 0}), 1, b"required section is missing"),
+        (dict(sections={2: 0}), 1, b"required section is missing"),
+        (dict(rows=21), 1, b"out of range"),
+        (dict(version=3), 5, b"unsupported format version"),
+    ]:
+        st, msg = _load(lib, _index_file(tmp_path / "bad.bin", **kwargs))
+        assert st == code and text in msg, (kwargs, st, msg)
