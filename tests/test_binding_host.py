@@ -9,6 +9,14 @@ import torch
 from paper_2404_00774_gb300 import binding
 
 
+@pytest.fixture(scope="module", autouse=True)
+def _library():
+    # the calls below load libsoar.so (host code only): build it if this
+    # module runs before any other that does
+    from paper_2404_00774_gb300 import build
+    build.build()
+
+
 def test_missing_library_raises_instead_of_falling_back(monkeypatch, tmp_path):
     monkeypatch.setattr(binding, "LIB_PATH", str(tmp_path / "libsoar.so"))
     monkeypatch.setattr(binding, "_lib", None)
