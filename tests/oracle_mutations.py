@@ -46,6 +46,8 @@ M = [
     ("ivf offsets shifted", SO, "offsets[1:] = np.cumsum(cnt)", "offsets[:-1] = np.cumsum(cnt)", 0),
     ("select sign", SO, "a, b = topk_desc(S[i], t)", "a, b = topk_desc(-S[i], t)", 0),
     ("ivf no dedup", SO, "mem = np.unique(mem).astype(np.int64)", "mem = mem.astype(np.int64)", 0),
+    ("ivf per-query counts ignored", SO, "tq = t if t_per_query is None else int(t_per_query[i])\n        parts = top[i, :tq]", "tq = t\n        parts = top[i, :tq]", 0),
+    ("pq per-query counts ignored", SO, "tq = t if t_per_query is None else int(t_per_query[i])\n        lut", "tq = t\n        lut", 0),
     ("ivf one probe short", SO, "parts = top[i, :tq]", "parts = top[i, :max(tq - 1, 1)]", 0),
     ("ivf wrong query", SO, "s = np.asarray(X[mem], dtype=F64) @ Q[i]", "s = np.asarray(X[mem], dtype=F64) @ Q[(i + 1) % nq]", 0),
     ("pq residual sign", SO, "np.asarray(X, dtype=np.float32) - np.asarray(C, dtype=np.float32)[np.asarray(part)]", "np.asarray(X, dtype=np.float32) + np.asarray(C, dtype=np.float32)[np.asarray(part)]", 0),

@@ -964,3 +964,65 @@ def test_kmeans_update_sums_in_fp64():
     C = oracle.kmeans(X, np.array([0]), 1)
     want = np.array([math.fsum(X[:, j].astype(np.float64)) / n for j in range(2)]).astype(np.float32)
     np.testing.assert_array_equal(C[0], want)
+
+
+# ------------------------------------------- IVF search by loops, edge cases
+
+def _ivf_by_loops(Q, X, C, offsets, ids, k, tq):
+    """One query's IVF search written out: partitions ranked by (-<q, c>, id),
+    the first tq probed, their members as a set (a spilled point once), exact
+    scores ranked by (-score, id), the first k kept, padded with (-1, -inf)."""
+    q = [float(v) for v in Q]
+    score = lambda v: sum(a * float(b) for a, b in zip(q, v))
+    order = sorted(range(len(C)), key=lambda p: (-score(C[p]), p))
+    members = set()
+    for p in order[:tq]:
+        members.update(int(i) for i in ids[offsets[p]:offsets[p + 1]])
+    ranked = sorted(((-score(X[i]), i) for i in members))[:k]
+    out = [(i, -s) for s, i in ranked]
+    return out + [(-1, -math.inf)] * (k - len(out))
+
+
+def test_ivf_search_by_loops_with_per_query_counts_padding_and_spills():
+    # two spills, so a point met in up to three probed partitions must count
+    # once; per-query probe counts 0 .. c, and k larger than a small union
+    rng = np.random.default_rng(48)
+    n, d, c = 90, 6, 9
+    X = rng.standard_normal((n, d))
+    Q = rng.standard_normal((12, d))
+    C = oracle.kmeans(X, rng.choice(n, c, replace=False), 3).astype(np.float64)
+    A = oracle.soar_assign(X, C, 1.0, 2)
+    off, ids = oracle.build_ivf(A, c)
+    tpq = np.array([0, 1, 2, 3, 9, 5, 1, 0, 4, 9, 2, 7])
+    for k in (5, 60):
+        got_i, got_s = oracle.ivf_search(Q, X, C, off, ids, k, 9, t_per_query=tpq)
+        for i in range(12):
+            want = _ivf_by_loops(Q[i], X, C, off, ids, k, int(tpq[i]))
+            assert got_i[i].tolist() == [w[0] for w in want], (k, i)
+            np.testing.assert_allclose(got_s[i], [w[1] for w in want], rtol=1e-12)
+            real = got_i[i][got_i[i] >= 0]
+            assert len(set(real.tolist())) == len(real)          # no point twice
+        assert np.all(got_i[[0, 7]] == -1) and np.all(np.isneginf(got_s[[0, 7]]))
+    # with t for every query the per-query form equals the plain one
+    np.testing.assert_array_equal(oracle.ivf_search(Q, X, C, off, ids, 5, 4, t_per_query=np.full(12, 4))[0],
+                                  oracle.ivf_search(Q, X, C, off, ids, 5, 4)[0])
+
+
+def test_pq_search_per_query_counts_by_loops():
+    # per-query probe counts (0 probes nothing): each row equals the loops
+    # at that query's own count
+    rng = np.random.default_rng(49)
+    X = rng.standard_normal((200, 6)).astype(np.float32)
+    Q = rng.standard_normal((6, 6)).astype(np.float32)
+    C = oracle.kmeans(X, rng.choice(200, 8, replace=False), 3)
+    A = oracle.soar_assign(X, C, 1.0, 1)
+    off, ids = oracle.build_ivf(A, 8)
+    part = np.repeat(np.arange(8), np.diff(off))
+    Rres = oracle.pq_residuals(X[ids], C, part)
+    B = oracle.pq_train(Rres, 3, rng.choice(Rres.shape[0], 16, replace=False))
+    codes = oracle.pq_index_codes(X, C, off, ids, B)
+    tpq = np.array([3, 0, 1, 8, 2, 5])
+    gi, _ = oracle.pq_search(Q, X, C, off, ids, B, codes, 4, 8, 12, t_per_query=tpq)
+    for q in range(6):
+        assert list(gi[q]) == _pq_search_by_loops(Q[q], X, C, off, ids, B, codes, 4, int(tpq[q]), 12)
+    assert list(gi[1]) == [-1] * 4
