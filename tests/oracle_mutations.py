@@ -80,6 +80,18 @@ M = [
     ("precision shortlist short", SO, "cand, _ = topk_desc(approx, rescore, mem)", "cand, _ = topk_desc(approx, max(rescore - 1, 1), mem)", 1),
     ("precision rescored by fp8", SO, "exact = np.asarray(X[cand], dtype=F64) @ Qf[i].astype(F64)", "exact = np.asarray(X[cand], dtype=F64) @ (q8[i].astype(F64) * F64(qs[i]))", 0),
     ("precision exact selection", SO, "top, _ = select_partitions_fp8(Qf, C, t)", "top, _ = select_partitions(Qf, C, t)", 0),
+    ("precision no dedup", SO, "mem = np.unique(np.concatenate([ids[offsets[p]:offsets[p + 1]] for p in parts])).astype(np.int64)", "mem = np.concatenate([ids[offsets[p]:offsets[p + 1]] for p in parts]).astype(np.int64)", 0),
+    ("kmr normalisation", SO, "return hits / (k * S.shape[0])", "return hits / S.shape[0]", 0),
+    ("fp8 sign dropped", SO, "return (np.sign(v) * q).astype(np.float32)", "return q.astype(np.float32)", 0),
+    ("fp8 codes unscaled", SO, "codes = fp8_e4m3_round((R / scale[:, None]).astype(np.float32))", "codes = fp8_e4m3_round(R.astype(np.float32))", 0),
+    ("bf16 truncation", SO, "u = (u + 0x7FFF + lsb) & 0xFFFF0000", "u = u & 0xFFFF0000", 0),
+    ("ivf sorted by point first", SO, "order = np.lexsort((pid, part))", "order = np.lexsort((part, pid))", 0),
+    ("kmeans seeds reversed", SO, "C = np.asarray(X[np.asarray(init_idx)], dtype=np.float32).copy()", "C = np.asarray(X[np.asarray(init_idx)[::-1]], dtype=np.float32).copy()", 0),
+    ("datapoints cumulative sizes", SO, "sizes = np.diff(np.asarray(offsets))", "sizes = np.asarray(offsets)[1:]", 0),
+    ("forward b3 sign", PM, "y = (h2 @ p[\"W3\"].T)[:, 0] + p[\"b3\"][0]", "y = (h2 @ p[\"W3\"].T)[:, 0] - p[\"b3\"][0]", 0),
+    ("backward W2 transposed", PM, "g[\"W2\"] = ga2.T @ h1", "g[\"W2\"] = h1.T @ ga2", 0),
+    ("adam no v bias correction", PM, "vh = v[name] / (1 - beta2 ** step)", "vh = v[name]", 0),
+    ("features drop the best", PM, "S = -np.sort(-S, axis=1)[:, :top]", "S = -np.sort(-S, axis=1)[:, 1:top + 1]", 0),
     ("features ascending", PM, "S = -np.sort(-S, axis=1)[:, :top]", "S = np.sort(S, axis=1)[:, ::-1][:, 1:top + 1] if S.shape[1] > top else -np.sort(-S, axis=1)[:, :top]", 0),
     ("features order swapped", PM, "np.concatenate([Q, S], axis=1)", "np.concatenate([S, Q], axis=1)", 0),
     ("forward relu1 dropped", PM, "h1 = np.maximum(a1, 0.0)", "h1 = a1", 0),
