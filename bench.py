@@ -322,6 +322,51 @@ def time_oracle(X, Q, C, off, ids, k, t, sample):
     return Qs.shape[0] / dt, dt, (time.process_time() - c0) / dt
 
 
+# the child process of time_oracle_one_core: its BLAS is limited to one
+# thread by the environment set before numpy loads; it regenerates the data
+# from the workload's seed, loads the parent's index and queries, and prints
+# the wall and CPU time of the oracle's search
+_ONE_CORE_CHILD = """
+import json, sys, time
+import numpy as np
+root, path, workload, k, t = sys.argv[1], sys.argv[2], sys.argv[3], int(sys.argv[4]), int(sys.argv[5])
+sys.path.insert(0, root)
+import oracle, synth
+a = np.load(path)
+w = synth.WORKLOADS[workload]
+X = synth.mixture_for(w).sample(w.n, w.data_seed)
+c0, t0 = time.process_time(), time.perf_counter()
+oracle.ivf_search(a["Q"], X, a["C"], a["off"], a["ids"], k, t)
+dt = time.perf_counter() - t0
+print(json.dumps({"secs": dt, "cpu_over_wall": (time.process_time() - c0) / dt}))
+"""
+
+
+def time_oracle_one_core(workload, Q, C, off, ids, k, t, sample):
+    """The oracle's search over ``sample`` queries on one core: a child
+    process with one BLAS thread, the index and queries handed over in a
+    temporary file.  Returns the cpu_baseline-style record, or a record with
+    an ``error`` when the child failed (the bench line is printed either
+    way)."""
+    import tempfile
+    Qs = np.asarray(Q[:sample])
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "oracle_index.npz")
+        np.savez(path, Q=Qs, C=np.asarray(C), off=np.asarray(off), ids=np.asarray(ids))
+        try:
+            r = subprocess.run([sys.executable, "-c", _ONE_CORE_CHILD, ROOT, path, workload, str(k), str(t)],
+                               env=env, capture_output=True, text=True, timeout=900)
+        except subprocess.TimeoutExpired:
+            return {"error": "one-core oracle run exceeded 900 s"}
+    if r.returncode != 0:
+        return {"error": (r.stderr.strip().splitlines() or ["exit %d" % r.returncode])[-1][:200]}
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": Qs.shape[0] / out["secs"], "unit": "queries/s", "cores": 1, "kind": "oracle",
+            "sample": f"{Qs.shape[0]} queries at t={t}, one BLAS thread ({out['secs']:.1f} s)",
+            "cpu_time_over_wall": out["cpu_over_wall"]}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -369,7 +414,9 @@ def run_reference(args):
                    "t": t, "queries_per_step": per_step, "index": "oracle's own (k-means on 300k rows)"},
         "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
                          "sample": f"{per_step} queries per step x {args.steps} steps, t={t}",
-                         "setup_s": setup, "cpu_time_over_wall": busy},
+                         "setup_s": setup, "cpu_time_over_wall": busy,
+                         "one_core": time_oracle_one_core(args.workload, Q, C, off, ids, w.k, t,
+                                                          max(16, args.cpu_sample // 3))},
         "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -1072,7 +1119,9 @@ def run_ours(args):
         cpu = {"value": qps_cpu, "unit": "queries/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"{min(args.cpu_sample, Q.shape[0])} queries at t={t_main} over the oracle's own "
                          f"index (fp64 numpy, {secs:.1f} s)", "setup_s": setup,
-               "cpu_time_over_wall": busy}
+               "cpu_time_over_wall": busy,
+               "one_core": time_oracle_one_core(args.workload, Q, Co, offo, idso, k, t_main,
+                                                max(16, args.cpu_sample // 3))}
 
     total_q = nq * world
     line = {

@@ -152,3 +152,16 @@ def test_time_oracle_reports_rate_wall_time_and_cpu_use():
     assert busy > 0
     qps_all, _, _ = bench.time_oracle(X, Q, C, off, ids, w.k, 4, 10_000)   # more than there are
     assert qps_all > 0
+
+
+def test_one_core_oracle_timing_runs_in_a_single_thread_child():
+    import synth
+    w = synth.WORKLOADS["tiny"]
+    X, Q, _ = synth.workload_arrays("tiny", nq=40)
+    C, off, ids = bench.oracle_index(X, w, w.lam, w.spills, train_rows=20_000, iters=2)
+    rec = bench.time_oracle_one_core("tiny", Q, C, off, ids, w.k, 4, 32)
+    assert "error" not in rec, rec
+    assert rec["cores"] == 1 and rec["value"] > 0 and rec["kind"] == "oracle"
+    assert rec["cpu_time_over_wall"] < 1.5                  # one thread did the work
+    bad = bench.time_oracle_one_core("no_such_workload", Q, C, off, ids, w.k, 4, 8)
+    assert set(bad) == {"error"} and "no_such_workload" in bad["error"]
