@@ -322,3 +322,42 @@ def test_binding_structs_have_the_c_layout(tmp_path):
             off, size = c_layout[(cname, field)]
             assert getattr(cls, field).offset == off, (cname, field)
             assert ct.sizeof(ftype) == size, (cname, field)
+
+
+def test_a_plain_c_program_links_and_calls_the_library(tmp_path):
+    # the boundary needs no Python or torch: a C client built from the header
+    # alone links libsoar.so and gets the documented statuses on the host
+    import shutil
+    import subprocess
+    from paper_2404_00774_gb300 import build
+    gcc = shutil.which("gcc")
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    cuda = os.path.dirname(os.path.dirname(os.path.realpath(nvcc)))
+    if not gcc or not os.path.exists(os.path.join(cuda, "include", "cuda_runtime_api.h")):
+        pytest.skip("gcc or the CUDA headers are missing")
+    lib = build.build()
+    src = tmp_path / "client.c"
+    src.write_text(r"""
+#include <stdio.h>
+#include <string.h>
+#include "soar.h"
+int main(void) {
+  int32_t out[4];
+  soar_status s = soar_assign(NULL, SOAR_F32, 10, 4, NULL, 4, 1.0f, 1, out, NULL);
+  if (s != SOAR_EINVAL || strstr(soar_last_error(), "null pointer") == NULL) return 1;
+  s = soar_index_free(NULL);
+  if (s != SOAR_OK) return 2;
+  if (soar_mlp_param_count(160, 256) != 107265) return 3;
+  printf("%s\n", soar_version());
+  return 0;
+}
+""")
+    exe = tmp_path / "client"
+    libdir = os.path.dirname(lib)
+    subprocess.run([gcc, "-std=c11", "-I", os.path.join(ROOT, "include"), "-I", os.path.join(cuda, "include"),
+                    str(src), "-o", str(exe), "-L", libdir, "-lsoar", "-Wl,-rpath," + libdir,
+                    "-L", os.path.join(cuda, "lib64"), "-Wl,-rpath," + os.path.join(cuda, "lib64")],
+                   check=True, capture_output=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, (r.returncode, r.stderr)
+    assert "sm_103a" in r.stdout
