@@ -232,7 +232,8 @@ SOAR_API soar_status soar_search(const soar_index* index, const void* Q, soar_dt
  * partitions hold fewer than t fine centroids the query probes only those.
  * ------------------------------------------------------------------ */
 
-/* Builds the coarse index of `index`: k-means over its c fine centroids
+/* Builds the coarse index of `index` (the second VQ level of App. A.4):
+ * k-means over its c fine centroids
  * (c2 clusters, `iters` Lloyd steps from the rows init_idx [c2] (device
  * int32, distinct, in [0, c)), fp64 update as soar_train_centroids), then
  * the primary and `spills` SOAR assignments with weight `lambda` (as
@@ -243,7 +244,8 @@ SOAR_API soar_status soar_index_build_coarse(const soar_index* index, int32_t c2
                                              const int32_t* init_idx, float lambda, int32_t spills,
                                              soar_index** out, cudaStream_t stream);
 
-/* The two-level selection alone.
+/* The two-level selection alone (App. A.4: partition selection as an IVF
+ * search over the centroids).
  *   coarse    a coarse index (rows = the fine centroids, fp32)
  *   Q         [nq][d] queries (dtype), device
  *   t, t1     fine partitions kept (1 <= t <= min(c, 1024)), coarse partitions
@@ -256,7 +258,8 @@ SOAR_API soar_status soar_select_partitions_multilevel(const soar_index* coarse,
                                                        int64_t nq, int32_t t, int32_t t1, int32_t* top_out,
                                                        float* score_out, int32_t* count_out, cudaStream_t stream);
 
-/* soar_search with the probed partitions chosen by the two-level selection:
+/* soar_search (Section 2.2, Section 3.5) with the probed partitions chosen
+ * by the two-level selection of App. A.4:
  * the query probes the fine partitions soar_select_partitions_multilevel
  * returns (fewer than t when fewer were found; none gives only padding).
  * `coarse` must be a coarse index of `index` (n == index's c, same d, fp32).
@@ -310,7 +313,8 @@ SOAR_API soar_status soar_pq_train(const void* X, soar_dtype dtype, int64_t n, i
                                    cudaStream_t stream);
 
 /*
- * soar_index_build with mode SOAR_SCORE_PQ4: every copy (point x in
+ * soar_index_build with mode SOAR_SCORE_PQ4 (Section 3.5 and App. A.3: only
+ * the compressed codes are duplicated): every copy (point x in
  * partition p) is encoded from x - C_p with the codebooks B [d/2][16][2]
  * (per subspace the nearest centre, the lower index on ties), two codes per
  * byte (the even subspace in the low nibble); the original vectors are
@@ -321,7 +325,8 @@ SOAR_API soar_status soar_index_build_pq(const void* X, soar_dtype dtype, int64_
                                          soar_index** out, cudaStream_t stream);
 
 /*
- * Per-row FP8-E4M3 quantisation used by SOAR_SCORE_FP8 indices:
+ * Per-row FP8-E4M3 quantisation used by SOAR_SCORE_FP8 indices (the
+ * compressed, duplicated form of the Section 3.5 layout analogue):
  * scale[i] = max_j |V[i][j]| / 448 (1 when the row is zero) and
  * codes[i][j] = e4m3(V[i][j] / scale[i]) rounded to nearest-even and
  * saturated to +-448.  Exposed so the codes can be checked bit for bit.
@@ -373,11 +378,14 @@ SOAR_API soar_status soar_select_partitions_static(const soar_index* index, cons
  */
 SOAR_API int64_t soar_mlp_param_count(int32_t d_in, int32_t hidden);
 
-/* Z_out [nq][d + top] fp32 features (top <= min(c, 8192)). */
+/* Z_out [nq][d + top] fp32 features z(q) above (an extension): the query,
+ * then its top-`top` centroid scores <q, C_i> of Section 2.2, descending
+ * (top <= min(c, 8192)). */
 SOAR_API soar_status soar_probe_features(const soar_index* index, const void* Q, soar_dtype dtype, int64_t nq,
                                          int32_t top, float* Z_out, cudaStream_t stream);
 
-/* labels_out [nq] int32: t*(q), the smallest probe count whose recall@k reaches
+/* labels_out [nq] int32 (an extension; recall@k of Section 2.1, probe order of
+ * Section 2.2): t*(q), the smallest probe count whose recall@k reaches
  * target_recall, given the query's exact top-k `truth_ids` [nq][k] (int64,
  * e.g. from soar_exact_mips).  A neighbour is found at probe count t when one
  * of its partitions has position <= t in the query's probe order (ties to the
@@ -386,23 +394,27 @@ SOAR_API soar_status soar_probe_labels(const soar_index* index, const void* Q, s
                                        const int64_t* truth_ids, int32_t k, float target_recall,
                                        int32_t* labels_out, cudaStream_t stream);
 
-/* y_out [batch] = network output for Z [batch][d_in]. */
+/* y_out [batch] = network output for Z [batch][d_in] (the MLP above, an
+ * extension). */
 SOAR_API soar_status soar_mlp_forward(const float* params, int32_t d_in, int32_t hidden, const float* Z,
                                       int32_t batch, int32_t bf16, float* y_out, cudaStream_t stream);
 
-/* grads_out (same layout as params) = d/dparams of mean((y - target)^2) over
+/* The MLP above (an extension): grads_out (same layout as params) =
+ * d/dparams of mean((y - target)^2) over
  * the batch; loss_out (device float, may be NULL) = that loss. */
 SOAR_API soar_status soar_mlp_backward(const float* params, int32_t d_in, int32_t hidden, const float* Z,
                                        const float* target, int32_t batch, int32_t bf16, float* grads_out,
                                        float* loss_out, cudaStream_t stream);
 
-/* One Adam step (bias-corrected, step counted from 1) on `count` parameters;
+/* Training the MLP above (an extension): one Adam step (bias-corrected, step
+ * counted from 1) on `count` parameters;
  * m1, m2 are the caller's moment buffers (start at zero). */
 SOAR_API soar_status soar_mlp_adam(float* params, const float* grads, float* m1, float* m2, int64_t count,
                                    int32_t step, float lr, float beta1, float beta2, float eps,
                                    cudaStream_t stream);
 
-/* t_out [batch] = clamp(ceil(alpha * exp(y)), 1, c): per-query probe counts
+/* The MLP above (an extension): t_out [batch] = clamp(ceil(alpha * exp(y)),
+ * 1, c), per-query probe counts
  * for soar_search's t_per_query. */
 SOAR_API soar_status soar_mlp_predict_probes(const float* params, int32_t d_in, int32_t hidden, const float* Z,
                                              int32_t batch, int32_t bf16, float alpha, int32_t c, int32_t* t_out,
